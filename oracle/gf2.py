@@ -1,0 +1,95 @@
+"""The self-consistent GF2 loop of the paper's supplement (steps 1-3).
+
+1. restricted HF reference (F_HF, P_HF, S) -- supplied by ``gf2_inputs``;
+2. build G(i w) by Eq. GF (Sigma = 0 and F = F_HF at the start);
+   2.a find mu giving the right particle number,
+   2.b rebuild F(P) by Eq. FockMatrix and update G; repeat 2.a-2.b to
+       self-consistency; transform G(i w) -> G(tau);
+3. build Sigma(tau) by Eq. Sigma, transform Sigma(tau) -> Sigma(i w) and go
+   back to 2 until the energy stops changing.
+
+Optional damping (the supplement damps P in the inner loop and Sigma(tau) in
+the outer loop without stating amounts): P <- a_P P_new + (1-a_P) P_old and
+Sigma <- a_S Sigma_new + (1-a_S) Sigma_old, both 1 (no damping) by default.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import dyson as dy
+from . import energy as en
+from .fock import fock
+from .sigma import sigma_tau
+from .transforms import iw_to_tau, sigma_expansion, tail_moments, tau_to_iw
+
+
+@dataclass
+class GF2State:
+    F: np.ndarray
+    mu: float
+    P: np.ndarray
+    G_iw: np.ndarray
+    Sigma_iw: np.ndarray = None
+    Sigma_tau: np.ndarray = None
+    sig1: np.ndarray = None
+    sig2: np.ndarray = None
+    energies: list = field(default_factory=list)
+
+
+def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-10, max_iter=200,
+               p_damping=1.0):
+    """Steps 2.a-2.b: alternate the mu search and the Fock rebuild to self-consistency."""
+    S, h, v = system.S, system.h, system.eri
+    P_old = None
+    for _ in range(max_iter):
+        mu, G, P, _ = dy.mu_search(S, F, Sigma_iw, sig1, sig2, system.n_elec, beta, n_iw)
+        if P_old is not None and p_damping < 1.0:
+            P = p_damping * P + (1.0 - p_damping) * P_old
+        F_new = fock(h, v, P)
+        if np.abs(F_new - F).max() < tol:
+            return F_new, mu, G, P
+        F, P_old = F_new, P
+    raise RuntimeError("inner loop did not converge")
+
+
+def energy(system, state, beta):
+    e1 = en.e_one_body(state.P, system.h, state.F)
+    e2 = 0.0
+    if state.Sigma_iw is not None:
+        e2 = en.e_two_body(state.G_iw, state.Sigma_iw, state.sig1, system.S, beta)
+    return system.e_nuc + e1 + e2, e1, e2
+
+
+def self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn=None):
+    """G(i w) -> G(tau) -> Sigma(tau) -> Sigma(i w) for the current state."""
+    mom = tail_moments(system.S, state.F, state.mu, state.sig1, state.sig2)
+    G_tau = iw_to_tau(state.G_iw, mom, beta, n_tau)
+    Sig_tau = (sigma_fn or sigma_tau)(G_tau, system.eri)
+    return G_tau, Sig_tau
+
+
+def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damping=1.0,
+        p_damping=1.0, inner_tol=1e-10, sigma_fn=None, callback=None):
+    """Full GF2; returns the final GF2State (energies[] holds (E, E1, E2) per iteration)."""
+    n = system.nbf
+    F, mu, G, P = inner_loop(system, F_start, None, None, None, beta, n_iw, inner_tol,
+                             p_damping=p_damping)
+    state = GF2State(F=F, mu=mu, P=P, G_iw=G, sig1=np.zeros((n, n)), sig2=np.zeros((n, n)))
+    state.energies.append(energy(system, state, beta))
+    for _ in range(max_outer):
+        _, Sig_tau = self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn)
+        if state.Sigma_tau is not None and sigma_damping < 1.0:
+            Sig_tau = sigma_damping * Sig_tau + (1.0 - sigma_damping) * state.Sigma_tau
+        state.Sigma_tau = Sig_tau
+        state.Sigma_iw = tau_to_iw(Sig_tau, beta, n_iw)
+        state.sig1, state.sig2 = sigma_expansion(Sig_tau, beta)
+        state.F, state.mu, state.G_iw, state.P = inner_loop(
+            system, state.F, state.Sigma_iw, state.sig1, state.sig2, beta, n_iw, inner_tol,
+            p_damping=p_damping)
+        state.energies.append(energy(system, state, beta))
+        if callback is not None:
+            callback(state)
+        if abs(state.energies[-1][0] - state.energies[-2][0]) < e_tol:
+            break
+    return state

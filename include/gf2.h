@@ -1,0 +1,166 @@
+/*
+ * libgf2 -- GB300 (sm_103a) library for the hot path of one self-consistent
+ * GF2 iteration (Phillips & Zgid, arXiv:1405.3273).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - N basis functions (real, non-orthogonal AO basis), closed shell.
+ *  - Matrices are dense row-major [N][N] FP64.  Integrals are chemists'
+ *    notation, v[i][j][k][l] = (ij|kl), dense [N][N][N][N] FP64 with the
+ *    8-fold permutational symmetry of real orbitals.
+ *  - Imaginary time: uniform grid tau_k = k*beta/M, k = 0..M, M = n_tau-1.
+ *    Tau-dependent matrices are [n_tau][N][N] FP64, real symmetric.
+ *  - Matsubara frequencies w_n = (2n+1)*pi/beta for n = 0..n_iw-1 (negative
+ *    frequencies follow from X(-iw) = conj X(iw)).  Frequency-dependent
+ *    matrices are [n_iw][N][N] complex128 stored as interleaved (re, im)
+ *    FP64 pairs.
+ *  - Transform conventions: X(iw) = int_0^beta e^{iw tau} X(tau) dtau and
+ *    X(tau) = (1/beta) sum_n e^{-iw tau} X(iw).  G is the per-spin Green's
+ *    function, P the spin-summed density (P = -2 G(beta^-)).
+ *
+ * Ownership and errors
+ * --------------------
+ *  - Every d_* argument is a DEVICE pointer owned by the caller; the library
+ *    never frees or retains it beyond the call (except gf2_set_integrals,
+ *    which copies).  Host scalars are returned through host pointers.
+ *  - The context owns its workspace (intermediates, split copies of the
+ *    integrals, grid tables) and allocates it at gf2_create /
+ *    gf2_set_integrals.  All work is stream-ordered on the context stream;
+ *    calls that return host scalars (gf2_mu_search, gf2_energy) synchronize
+ *    that stream.
+ *  - Every call returns a gf2_status.  Invalid sizes or NULL pointers give
+ *    GF2_ERR_ARG before any launch; a CUDA failure gives GF2_ERR_CUDA; device
+ *    loops that give up after their iteration limit report GF2_ERR_TIMEOUT.
+ *    gf2_last_error() returns a message for the last failure on the context.
+ *    No call aborts the process or throws across the ABI.
+ */
+#ifndef GF2_H
+#define GF2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GF2_OK = 0,
+  GF2_ERR_ARG = 1,
+  GF2_ERR_CUDA = 2,
+  GF2_ERR_NOMEM = 3,
+  GF2_ERR_NOT_CONVERGED = 4,
+  GF2_ERR_TIMEOUT = 5,
+  GF2_ERR_NONFINITE = 6,
+  GF2_ERR_UNSUPPORTED = 7
+} gf2_status;
+
+/* Arithmetic of the self-energy contraction.
+ *   GF2_PREC_FP64    FP64 everywhere (CUDA cores).
+ *   GF2_PREC_BF16X3  every operand split x = x_hi + x_lo into two BF16 terms,
+ *                    three products hi*hi + hi*lo + lo*hi per multiply, FP32
+ *                    accumulation on the tcgen05 tensor cores, FP64 for the
+ *                    final sum over each block of the last contraction.
+ *   GF2_PREC_BF16X6  three BF16 terms, six products (i + j <= 2). */
+typedef enum {
+  GF2_PREC_FP64 = 0,
+  GF2_PREC_BF16X3 = 1,
+  GF2_PREC_BF16X6 = 2
+} gf2_prec;
+
+typedef struct gf2_ctx gf2_ctx;
+
+/* Create a context for N basis functions (1 <= N <= 112), n_tau time points
+ * (M = n_tau - 1 a power of two, 8 <= M <= 16384), n_iw >= 1 Matsubara
+ * frequencies and inverse temperature
+ * beta > 0, bound to the CUDA stream `stream` (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  *out receives the context. */
+gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, double beta, void *stream);
+gf2_status gf2_destroy(gf2_ctx *ctx);
+gf2_status gf2_set_stream(gf2_ctx *ctx, void *stream);
+const char *gf2_status_string(gf2_status s);
+const char *gf2_last_error(const gf2_ctx *ctx);
+
+/* Copy the two-electron integrals v [N^4] into the context and build the
+ * exchange combination W_lpnj = 2 v_lpnj - v_nplj of Eq. Sigma plus its BF16
+ * split copies for the tensor-core path. */
+gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v);
+
+/* Eq. Sigma (the paper's second-order self-energy):
+ *   Sigma_ij(tau) = - sum_klmnpq G_kl(tau) G_mn(tau) G_pq(-tau) v_imqk (2 v_lpnj - v_nplj)
+ * with G(-tau_k) = -G(tau_{M-k}).  d_G_tau [n_tau][N][N] in, d_Sigma_tau
+ * [n_tau][N][N] out.  Requires gf2_set_integrals first. */
+gf2_status gf2_sigma_tau(gf2_ctx *ctx, const double *d_G_tau, double *d_Sigma_tau, int prec);
+
+/* The same for the `count` grid points k0 .. k0+count-1 only: d_G_tau is the
+ * full [n_tau][N][N] grid (G(-tau) needs the mirrored points), d_Sigma_out
+ * receives [count][N][N]. */
+gf2_status gf2_sigma_tau_points(gf2_ctx *ctx, const double *d_G_tau, int k0, int count,
+                                double *d_Sigma_out, int prec);
+
+/* High-frequency moments G1..G4 of G(z) = [(z + mu) S - F - Sigma(z)]^-1 for
+ * Sigma(z) ~ Sig1/z + Sig2/z^2 (the analytic tail named in the paper's
+ * section on the Fourier transforms):
+ *   G1 = S^-1, G2 = S^-1 X S^-1, G3 = S^-1 (X S^-1 X + Sig1) S^-1,
+ *   G4 = S^-1 (X S^-1 X S^-1 X + X S^-1 Sig1 + Sig1 S^-1 X + Sig2) S^-1,
+ * X = F - mu S.  d_sig12 = [2][N][N] (Sig1, Sig2) or NULL for zero.
+ * d_moments receives [4][N][N]. */
+gf2_status gf2_tail_moments(gf2_ctx *ctx, const double *d_S, const double *d_F, double mu,
+                            const double *d_sig12, double *d_moments);
+
+/* Matsubara -> imaginary time (G(w) -> G(tau) of step 2.b):
+ *   X(tau_k) = (2/beta) sum_{n<n_iw} Re[e^{-i w_n tau_k} (X - T)(i w_n)] + T(tau_k),
+ * T = the moment series of d_moments [4][N][N] resummed about a real pole
+ * a = 1 hartree, T(z) = sum_r c_r (z - a)^-r, whose tau image is closed form.
+ * Evaluated by one M-point FFT per matrix element (n_iw may exceed M; the
+ * frequencies are folded modulo M).  d_X_iw [n_iw][N][N] c128 in,
+ * d_X_tau [n_tau][N][N] out. */
+gf2_status gf2_fft_iw_to_tau(gf2_ctx *ctx, const double *d_X_iw, const double *d_moments,
+                             double *d_X_tau);
+
+/* Imaginary time -> Matsubara (Sigma(tau) -> Sigma(w) of step 3):
+ *   X(i w_n) = int_0^beta e^{i w_n tau} X~(tau) dtau,
+ * X~ = the piecewise-cubic interpolant of the samples (on [tau_a, tau_a+1]
+ * the cubic through nodes a-1..a+2; nodes 0..3 and M-3..M at the ends),
+ * integrated exactly: an M-point FFT times an attenuation factor plus
+ * end-point corrections.  d_X_tau [n_tau][N][N] in, d_X_iw [n_iw][N][N] c128
+ * out.  If d_sig12 is not NULL it receives [2][N][N] = (Sig1, Sig2), the
+ * 1/z and 1/z^2 coefficients of the result: Sig1 = -(X(0) + X(beta)),
+ * Sig2 = X~'(0+) + X~'(beta-). */
+gf2_status gf2_fft_tau_to_iw(gf2_ctx *ctx, const double *d_X_tau, double *d_X_iw, double *d_sig12);
+
+/* Eq. GF: G(i w_n) = [(i w_n + mu) S - F - Sigma(i w_n)]^-1 for every n
+ * (FP64 complex; d_Sigma_iw may be NULL for Sigma = 0). */
+gf2_status gf2_dyson(gf2_ctx *ctx, double mu, const double *d_S, const double *d_F,
+                     const double *d_Sigma_iw, double *d_G_iw);
+
+/* Spin-summed density P = -2 G(beta^-) = (4/beta) sum_n Re (G - T)(i w_n) - 2 T(beta),
+ * with T built from d_moments [4][N][N] as in gf2_fft_iw_to_tau. */
+gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_moments, double *d_P);
+
+/* Step 2.a: find mu with Tr(P(mu) S) = n_elec to |error| <= tol, P(mu) from
+ * Eq. GF and gf2_density.  Bracketing search started at *mu_inout (expanded
+ * outward until it brackets), then Illinois false position with bisection
+ * safeguards; at most max_iter evaluations (GF2_ERR_NOT_CONVERGED beyond).
+ * On success *mu_inout = mu, d_G_iw and d_P hold G(i w) and P at that mu,
+ * *n_eval (if not NULL) = number of Dyson evaluations.  Synchronizes. */
+gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
+                         const double *d_Sigma_iw, const double *d_sig12, double n_elec,
+                         double tol, int max_iter, double *mu_inout, double *d_G_iw,
+                         double *d_P, int *n_eval);
+
+/* Eq. FockMatrix: F_ij = h_ij + sum_kl P_kl (v_ijlk - v_iklj / 2), with the
+ * integrals given to gf2_set_integrals. */
+gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_P, double *d_F);
+
+/* Galitskii-Migdal energy (the paper reports energies but prints no formula):
+ *   e_one_body = (1/2) Tr[P (h + F)]
+ *   e_two_body = (2/beta) sum_{n<n_iw} Re Tr[G(i w_n) Sigma(i w_n)]
+ *                - beta/(2 pi^2) psi_1(n_iw + 1/2) Tr[S^-1 Sig1]
+ * (the second term completes the sum over n >= n_iw with G Sigma ~ G1 Sig1 / z^2).
+ * d_sig12 may be NULL (no tail).  Synchronizes. */
+gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *d_F, const double *d_P,
+                      const double *d_S, const double *d_G_iw, const double *d_Sigma_iw,
+                      const double *d_sig12, double *e_one_body, double *e_two_body);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF2_H */

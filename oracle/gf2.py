@@ -47,9 +47,12 @@ def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-10, max_iter=
         if P_old is not None and p_damping < 1.0:
             P = p_damping * P + (1.0 - p_damping) * P_old
         F_new = fock(h, v, P)
-        if np.abs(F_new - F).max() < tol:
-            return F_new, mu, G, P
+        converged = np.abs(F_new - F).max() < tol
         F, P_old = F_new, P
+        if converged:
+            # G, P and mu evaluated at the converged F
+            mu, G, P, _ = dy.mu_search(S, F, Sigma_iw, sig1, sig2, system.n_elec, beta, n_iw)
+            return F, mu, G, P
     raise RuntimeError("inner loop did not converge")
 
 

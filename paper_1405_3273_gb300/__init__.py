@@ -1,0 +1,199 @@
+"""Python binding of libgf2, the GB300 library for the hot path of one
+self-consistent GF2 iteration (second-order self-energy, Matsubara/tau
+transforms, Dyson solve, chemical-potential search, Fock build and energy).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name in ``libgf2.so`` (declared in ``include/gf2.h``) with device
+pointers taken from CUDA torch tensors and the current torch stream.  There is
+no CPU fallback: importing works without a GPU, but calling any function needs
+the built library and a CUDA device, and fails loudly otherwise.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgf2.so")
+
+GF2_OK = 0
+GF2_PREC_FP64 = 0
+GF2_PREC_BF16X3 = 1
+GF2_PREC_BF16X6 = 2
+STATUS_NAMES = {0: "GF2_OK", 1: "GF2_ERR_ARG", 2: "GF2_ERR_CUDA", 3: "GF2_ERR_NOMEM",
+                4: "GF2_ERR_NOT_CONVERGED", 5: "GF2_ERR_TIMEOUT", 6: "GF2_ERR_NONFINITE",
+                7: "GF2_ERR_UNSUPPORTED"}
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "gf2_create": [ctypes.POINTER(_P), _I, _I, _I, _D, _P],
+    "gf2_destroy": [_P],
+    "gf2_set_stream": [_P, _P],
+    "gf2_status_string": [_I],
+    "gf2_last_error": [_P],
+    "gf2_set_integrals": [_P, _P],
+    "gf2_sigma_tau": [_P, _P, _P, _I],
+    "gf2_sigma_tau_points": [_P, _P, _I, _I, _P, _I],
+    "gf2_tail_moments": [_P, _P, _P, _D, _P, _P],
+    "gf2_fft_iw_to_tau": [_P, _P, _P, _P],
+    "gf2_fft_tau_to_iw": [_P, _P, _P, _P],
+    "gf2_dyson": [_P, _D, _P, _P, _P, _P],
+    "gf2_density": [_P, _P, _P, _P],
+    "gf2_mu_search": [_P, _P, _P, _P, _P, _D, _D, _I, ctypes.POINTER(_D), _P, _P, ctypes.POINTER(_I)],
+    "gf2_fock": [_P, _P, _P, _P],
+    "gf2_energy": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+}
+
+
+class GF2Error(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib():
+    """The loaded libgf2 (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgf2.so not built at {LIB_PATH}; run paper_1405_3273_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("gf2_status_string", "gf2_last_error") else _I
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(status, ctx):
+    if status != GF2_OK:
+        msg = lib().gf2_last_error(ctx).decode() if ctx else lib().gf2_status_string(status).decode()
+        raise GF2Error(status, msg)
+
+
+_F64 = torch.float64
+_C128 = torch.complex128
+
+
+def gf2_create(n_bf, n_tau, n_iw, beta):
+    h = ctypes.c_void_p()
+    st = lib().gf2_create(ctypes.byref(h), int(n_bf), int(n_tau), int(n_iw), float(beta), _stream())
+    if st != GF2_OK:
+        raise GF2Error(st, "gf2_create rejected the sizes or could not allocate")
+    return h
+
+
+def gf2_destroy(ctx):
+    _check(lib().gf2_destroy(ctx), None)
+
+
+def gf2_set_stream(ctx):
+    _check(lib().gf2_set_stream(ctx, _stream()), ctx)
+
+
+def gf2_set_integrals(ctx, v):
+    _check(lib().gf2_set_integrals(ctx, _ptr(v, _F64)), ctx)
+
+
+def gf2_sigma_tau(ctx, G_tau, Sigma_tau, prec=GF2_PREC_FP64):
+    _check(lib().gf2_sigma_tau(ctx, _ptr(G_tau, _F64), _ptr(Sigma_tau, _F64), int(prec)), ctx)
+
+
+def gf2_sigma_tau_points(ctx, G_tau, k0, count, Sigma_out, prec=GF2_PREC_FP64):
+    _check(lib().gf2_sigma_tau_points(ctx, _ptr(G_tau, _F64), int(k0), int(count),
+                                      _ptr(Sigma_out, _F64), int(prec)), ctx)
+
+
+def gf2_tail_moments(ctx, S, F, mu, sig12, moments):
+    _check(lib().gf2_tail_moments(ctx, _ptr(S, _F64), _ptr(F, _F64), float(mu), _ptr(sig12, _F64),
+                                  _ptr(moments, _F64)), ctx)
+
+
+def gf2_fft_iw_to_tau(ctx, X_iw, moments, X_tau):
+    _check(lib().gf2_fft_iw_to_tau(ctx, _ptr(X_iw, _C128), _ptr(moments, _F64), _ptr(X_tau, _F64)), ctx)
+
+
+def gf2_fft_tau_to_iw(ctx, X_tau, X_iw, sig12=None):
+    _check(lib().gf2_fft_tau_to_iw(ctx, _ptr(X_tau, _F64), _ptr(X_iw, _C128), _ptr(sig12, _F64)), ctx)
+
+
+def gf2_dyson(ctx, mu, S, F, Sigma_iw, G_iw):
+    _check(lib().gf2_dyson(ctx, float(mu), _ptr(S, _F64), _ptr(F, _F64), _ptr(Sigma_iw, _C128),
+                           _ptr(G_iw, _C128)), ctx)
+
+
+def gf2_density(ctx, G_iw, moments, P):
+    _check(lib().gf2_density(ctx, _ptr(G_iw, _C128), _ptr(moments, _F64), _ptr(P, _F64)), ctx)
+
+
+def gf2_mu_search(ctx, S, F, Sigma_iw, sig12, n_elec, mu0, G_iw, P, tol=1e-10, max_iter=100):
+    mu = ctypes.c_double(float(mu0))
+    nev = ctypes.c_int(0)
+    _check(lib().gf2_mu_search(ctx, _ptr(S, _F64), _ptr(F, _F64), _ptr(Sigma_iw, _C128),
+                               _ptr(sig12, _F64), float(n_elec), float(tol), int(max_iter),
+                               ctypes.byref(mu), _ptr(G_iw, _C128), _ptr(P, _F64),
+                               ctypes.byref(nev)), ctx)
+    return mu.value, nev.value
+
+
+def gf2_fock(ctx, h, P, F):
+    _check(lib().gf2_fock(ctx, _ptr(h, _F64), _ptr(P, _F64), _ptr(F, _F64)), ctx)
+
+
+def gf2_energy(ctx, h, F, P, S, G_iw, Sigma_iw, sig12):
+    e1, e2 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().gf2_energy(ctx, _ptr(h, _F64), _ptr(F, _F64), _ptr(P, _F64), _ptr(S, _F64),
+                            _ptr(G_iw, _C128), _ptr(Sigma_iw, _C128), _ptr(sig12, _F64),
+                            ctypes.byref(e1), ctypes.byref(e2)), ctx)
+    return e1.value, e2.value
+
+
+class Context:
+    """Owning handle around a gf2_ctx (destroyed on close / garbage collection)."""
+
+    def __init__(self, n_bf, n_tau, n_iw, beta):
+        self.n_bf, self.n_tau, self.n_iw, self.beta = int(n_bf), int(n_tau), int(n_iw), float(beta)
+        self.handle = gf2_create(n_bf, n_tau, n_iw, beta)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gf2_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

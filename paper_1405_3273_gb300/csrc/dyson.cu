@@ -1,0 +1,465 @@
+// Eq. GF (per-frequency Dyson inverse), the density matrix, the chemical
+// potential search (step 2.a), Eq. FockMatrix (step 2.b), the tail moments of
+// G and the Galitskii-Migdal energy, all in FP64.
+//
+// Tail moments.  With X = F - mu S the moments are polynomials in mu:
+//   G1 = A0,  G2 = A1 - mu A0,  G3 = A2 - 2mu A1 + mu^2 A0 + B1,
+//   G4 = A3 - 3mu A2 + 3mu^2 A1 - mu^3 A0 + B2 - 2mu B1 + B3,
+// A0 = S^-1, A_{r+1} = S^-1 F A_r, B1 = S^-1 Sig1 S^-1,
+// B2 = S^-1 F B1 + B1 F S^-1, B3 = S^-1 Sig2 S^-1,
+// so one set of N^3 products per (F, Sig1, Sig2) serves every mu of a search.
+//
+// Dyson.  A(i w) = (i w + mu) S - F - Sigma(i w) is complex symmetric with
+// Im A = w S - Im Sigma positive definite for w > 0 (Im Sigma(i w) <= 0 for a
+// causal self-energy), so Gauss-Jordan elimination without pivoting is stable;
+// pivots are still checked and a tiny one is reported as GF2_ERR_NONFINITE.
+// One CTA per frequency, the matrix held in shared memory.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gf2_internal.cuh"
+
+namespace {
+
+enum { SL_SINV = GF2_SL_SINV, SL_A1 = GF2_SL_A1, SL_A2 = GF2_SL_A2, SL_A3 = GF2_SL_A3,
+       SL_B1 = GF2_SL_B1, SL_B2 = GF2_SL_B2, SL_B3 = GF2_SL_B3, SL_T1 = GF2_SL_T1, SL_TMP = GF2_SL_TMP,
+       SL_MOM = GF2_SL_MOM, SL_COEF = GF2_SL_COEF, SL_MISC = GF2_SL_MISC };
+
+__global__ void pole_coef_kernel(int N2, double a, const double *mom, double *coef) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N2) return;
+  const double g1 = mom[e], g2 = mom[N2 + e], g3 = mom[2 * N2 + e], g4 = mom[3 * N2 + e];
+  coef[e] = g1;
+  coef[N2 + e] = g2 - a * g1;
+  coef[2 * N2 + e] = g3 - 2.0 * a * g2 + a * a * g1;
+  coef[3 * N2 + e] = g4 - 3.0 * a * g3 + 3.0 * a * a * g2 - a * a * a * g1;
+}
+
+__global__ void moments_kernel(int N2, double mu, const double *basis, double *mom) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N2) return;
+  const double A0 = basis[SL_SINV * N2 + e], A1 = basis[SL_A1 * N2 + e];
+  const double A2 = basis[SL_A2 * N2 + e], A3 = basis[SL_A3 * N2 + e];
+  const double B1 = basis[SL_B1 * N2 + e], B2 = basis[SL_B2 * N2 + e], B3 = basis[SL_B3 * N2 + e];
+  mom[e] = A0;
+  mom[N2 + e] = A1 - mu * A0;
+  mom[2 * N2 + e] = A2 - 2.0 * mu * A1 + mu * mu * A0 + B1;
+  mom[3 * N2 + e] = A3 - 3.0 * mu * A2 + 3.0 * mu * mu * A1 - mu * mu * mu * A0 + B2 - 2.0 * mu * B1 + B3;
+}
+
+__global__ void dyson_kernel(int N, double beta, double mu, const double *__restrict__ S,
+                             const double *__restrict__ F, const double2 *__restrict__ Sig,
+                             double2 *__restrict__ G, int *flag) {
+  extern __shared__ double2 sm[];
+  const int N2 = N * N;
+  double2 *a = sm, *col = sm + N2, *row = col + N;
+  const long long n = blockIdx.x;
+  const double w = (2.0 * n + 1.0) * M_PI / beta;
+  for (int e = threadIdx.x; e < N2; e += blockDim.x) {
+    const double s = S[e];
+    double2 v = make_double2(mu * s - F[e], w * s);
+    if (Sig) v = csub(v, Sig[n * N2 + e]);
+    a[e] = v;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < N; ++k) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) col[i] = a[i * N + k];
+    __syncthreads();
+    const double2 piv = col[k];
+    const double mag = fabs(piv.x) + fabs(piv.y);
+    if (!(mag > 1e-280)) bad = true;
+    const double2 p = crecip(piv);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const double2 r = (j == k) ? p : cmul(a[k * N + j], p);
+      row[j] = r;
+      a[k * N + j] = r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N2; e += blockDim.x) {
+      const int i = e / N, j = e - i * N;
+      if (i == k) continue;
+      if (j == k) {
+        const double2 t = cmul(col[i], p);
+        a[e] = make_double2(-t.x, -t.y);
+      } else {
+        a[e] = csub(a[e], cmul(col[i], row[j]));
+      }
+    }
+    __syncthreads();
+  }
+  if (bad && threadIdx.x == 0) atomicExch(flag, 1);
+  for (int e = threadIdx.x; e < N2; e += blockDim.x) G[n * N2 + e] = a[e];
+}
+
+// partial[chunk][e] = sum_{n in chunk} Re G_e(n)
+__global__ void density_partial_kernel(int N2, int n_iw, int chunk, const double2 *__restrict__ G,
+                                       double *__restrict__ partial) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N2) return;
+  const int c = blockIdx.y;
+  const int n0 = c * chunk, n1 = min(n_iw, n0 + chunk);
+  double acc = 0.0;
+  for (int n = n0; n < n1; ++n) acc += G[(size_t)n * N2 + e].x;
+  partial[(size_t)c * N2 + e] = acc;
+}
+
+// P_e = (4/beta) [sum_n Re G_e - sum_r c_r R_r] - 2 sum_r c_r g_r(beta)
+__global__ void density_final_kernel(int N2, int nchunks, double beta, const double *partial,
+                                     const double *coef, const double *pole_resum,
+                                     const double *tau_pole_beta, double *P) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N2) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * N2 + e];
+  double tail_sum = 0.0, tail_beta = 0.0;
+  for (int r = 0; r < 4; ++r) {
+    const double cr = coef[(size_t)r * N2 + e];
+    tail_sum += cr * pole_resum[r];
+    tail_beta += cr * tau_pole_beta[r];
+  }
+  P[e] = (4.0 / beta) * (s - tail_sum) - 2.0 * tail_beta;
+}
+
+// out[0] = sum_ij P_ij S_ji (single CTA, fixed order)
+__global__ void trace_kernel(int N, const double *P, const double *S, double *out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    acc += P[e] * S[j * N + i];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// F_ij = h_ij + sum_kl P_kl (v_ijlk - v_iklj / 2), with v_ijlk = v_lkij (real ERIs)
+__global__ void fock_kernel(int N, const double *__restrict__ h, const double *__restrict__ v,
+                            const double *__restrict__ P, double *__restrict__ F) {
+  const int i = blockIdx.x, j = threadIdx.x;
+  if (j >= N) return;
+  const long long N2 = (long long)N * N, N3 = N2 * N;
+  double acc = 0.0;
+  for (int k = 0; k < N; ++k)
+    for (int l = 0; l < N; ++l) {
+      const double p = P[k * N + l];
+      const double coul = v[(long long)l * N3 + (long long)k * N2 + (long long)i * N + j];   // v_lkij
+      const double exch = v[(long long)i * N3 + (long long)k * N2 + (long long)l * N + j];   // v_iklj
+      acc += p * (coul - 0.5 * exch);
+    }
+  F[i * N + j] = h[i * N + j] + acc;
+}
+
+// partial[n] = sum_ij Re(G_ij Sigma_ji) at frequency n (32x32 tiles through smem)
+__global__ void energy_partial_kernel(int N, const double2 *__restrict__ G, const double2 *__restrict__ Sig,
+                                      double *__restrict__ partial) {
+  __shared__ double2 st[32][33];
+  __shared__ double red[256];
+  const long long n = blockIdx.x;
+  const size_t base = (size_t)n * N * N;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  double acc = 0.0;
+  for (int ib = 0; ib < N; ib += 32)
+    for (int jb = 0; jb < N; jb += 32) {
+      // stage Sigma[jb + r][ib + c] into st[r][c]
+      for (int r = ty; r < 32; r += 8) {
+        const int jj = jb + r, ii = ib + tx;
+        st[r][tx] = (jj < N && ii < N) ? Sig[base + (size_t)jj * N + ii] : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      for (int r = ty; r < 32; r += 8) {
+        const int ii = ib + r, jj = jb + tx;
+        if (ii < N && jj < N) {
+          const double2 g = G[base + (size_t)ii * N + jj];
+          const double2 s = st[tx][r];  // Sigma[jj][ii]
+          acc += g.x * s.x - g.y * s.y;
+        }
+      }
+      __syncthreads();
+    }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[n] = red[0];
+}
+
+__device__ double trigamma(double x) {
+  double acc = 0.0;
+  while (x < 20.0) {
+    acc += 1.0 / (x * x);
+    x += 1.0;
+  }
+  const double ix = 1.0 / x, ix2 = ix * ix;
+  return acc + ix + 0.5 * ix2 +
+         ix * ix2 * (1.0 / 6.0 - ix2 * (1.0 / 30.0 - ix2 * (1.0 / 42.0 - ix2 * (1.0 / 30.0 - ix2 * (5.0 / 66.0)))));
+}
+
+// out[0] = E1 = 1/2 Tr[P(h+F)], out[1] = E2 incl. tail
+__global__ void energy_final_kernel(int N, int n_iw, double beta, const double *partial, const double *P,
+                                    const double *h, const double *F, const double *Sinv,
+                                    const double *sig1, double *out) {
+  __shared__ double r1[256], r2[256], r3[256];
+  double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int n = threadIdx.x; n < n_iw; n += blockDim.x) a2 += partial[n];
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    a1 += P[e] * (h[j * N + i] + F[j * N + i]);
+    if (sig1) a3 += Sinv[e] * sig1[j * N + i];
+  }
+  r1[threadIdx.x] = a1;
+  r2[threadIdx.x] = a2;
+  r3[threadIdx.x] = a3;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      r1[threadIdx.x] += r1[threadIdx.x + s];
+      r2[threadIdx.x] += r2[threadIdx.x + s];
+      r3[threadIdx.x] += r3[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = 0.5 * r1[0];
+    double e2 = (2.0 / beta) * r2[0];
+    if (sig1) e2 -= beta / (2.0 * M_PI * M_PI) * trigamma(n_iw + 0.5) * r3[0];
+    out[1] = e2;
+  }
+}
+
+// ---------------- host helpers ----------------
+
+double *slot(gf2_ctx *ctx, int s) { return ctx->d_small + (size_t)s * ctx->N * ctx->N; }
+
+Dgemm square_gemm(int N, const double *A, const double *B, double *C, double alpha, double beta_c,
+                  bool transB = false) {
+  Dgemm g{};
+  g.M = N; g.N = N; g.K = N;
+  g.A = A; g.a_rs = N; g.a_cs = 1;
+  g.B = B; g.b_rs = transB ? 1 : N; g.b_cs = transB ? N : 1;
+  g.C = C; g.c_rs = N; g.c_cs = 1;
+  g.nb0 = 1; g.nb1 = 1; g.alpha = alpha; g.beta_c = beta_c; g.split_k = 1;
+  return g;
+}
+
+// moment basis A0..A3, B1..B3 into the small slots
+gf2_status build_moment_basis(gf2_ctx *ctx, const double *S, const double *F, const double *sig12) {
+  const int N = ctx->N;
+  const size_t N2 = (size_t)N * N;
+  gf2_status st;
+  if ((st = gf2_inverse_spd(ctx, S, slot(ctx, SL_SINV))) != GF2_OK) return st;
+  double *Sinv = slot(ctx, SL_SINV), *T1 = slot(ctx, SL_T1), *tmp = slot(ctx, SL_TMP);
+  if ((st = gf2_dgemm(ctx, square_gemm(N, Sinv, F, T1, 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, T1, Sinv, slot(ctx, SL_A1), 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, T1, slot(ctx, SL_A1), slot(ctx, SL_A2), 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, T1, slot(ctx, SL_A2), slot(ctx, SL_A3), 1.0, 0.0))) != GF2_OK) return st;
+  if (!sig12) {
+    GF2_CK(ctx, cudaMemsetAsync(slot(ctx, SL_B1), 0, 3 * N2 * sizeof(double), ctx->stream));
+    return GF2_OK;
+  }
+  const double *sig1 = sig12, *sig2 = sig12 + N2;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, sig1, Sinv, tmp, 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, Sinv, tmp, slot(ctx, SL_B1), 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, T1, slot(ctx, SL_B1), slot(ctx, SL_B2), 1.0, 0.0))) != GF2_OK) return st;
+  // B2 += B1 (S^-1 F)^T  (= B1 F S^-1 for symmetric S, F)
+  if ((st = gf2_dgemm(ctx, square_gemm(N, slot(ctx, SL_B1), T1, slot(ctx, SL_B2), 1.0, 1.0, true))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, sig2, Sinv, tmp, 1.0, 0.0))) != GF2_OK) return st;
+  if ((st = gf2_dgemm(ctx, square_gemm(N, Sinv, tmp, slot(ctx, SL_B3), 1.0, 0.0))) != GF2_OK) return st;
+  return GF2_OK;
+}
+
+gf2_status launch_moments(gf2_ctx *ctx, double mu, double *mom) {
+  const int N2 = ctx->N * ctx->N;
+  moments_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(N2, mu, ctx->d_small, mom);
+  GF2_CK_LAUNCH(ctx, "moments_kernel");
+  return GF2_OK;
+}
+
+gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *F, const double *Sig,
+                        double *G) {
+  const int N = ctx->N;
+  const size_t smem = sizeof(double2) * ((size_t)N * N + 2 * N);
+  GF2_CK(ctx, cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  dyson_kernel<<<ctx->n_iw, 256, smem, ctx->stream>>>(N, ctx->beta, mu, S, F,
+                                                       reinterpret_cast<const double2 *>(Sig),
+                                                       reinterpret_cast<double2 *>(G), ctx->d_err);
+  GF2_CK_LAUNCH(ctx, "dyson_kernel");
+  return GF2_OK;
+}
+
+gf2_status launch_density(gf2_ctx *ctx, const double *G, const double *coef, double *P) {
+  const int N2 = ctx->N * ctx->N;
+  const int chunk = 256;
+  const int nchunks = (ctx->n_iw + chunk - 1) / chunk;
+  dim3 grid((N2 + 127) / 128, nchunks);
+  density_partial_kernel<<<grid, 128, 0, ctx->stream>>>(N2, ctx->n_iw, chunk,
+                                                         reinterpret_cast<const double2 *>(G), ctx->d_red);
+  GF2_CK_LAUNCH(ctx, "density_partial_kernel");
+  density_final_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(
+      N2, nchunks, ctx->beta, ctx->d_red, coef, ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M, P);
+  GF2_CK_LAUNCH(ctx, "density_final_kernel");
+  return GF2_OK;
+}
+
+}  // namespace
+
+gf2_status gf2_pole_coefficients(gf2_ctx *ctx, const double *d_moments, double *d_coef) {
+  const int N2 = ctx->N * ctx->N;
+  pole_coef_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(N2, GF2_TAIL_POLE, d_moments, d_coef);
+  GF2_CK_LAUNCH(ctx, "pole_coef_kernel");
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_tail_moments(gf2_ctx *ctx, const double *d_S, const double *d_F, double mu,
+                                       const double *d_sig12, double *d_moments) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_S || !d_F || !d_moments) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_tail_moments: NULL pointer");
+  gf2_status st = build_moment_basis(ctx, d_S, d_F, d_sig12);
+  if (st != GF2_OK) return st;
+  return launch_moments(ctx, mu, d_moments);
+}
+
+extern "C" gf2_status gf2_dyson(gf2_ctx *ctx, double mu, const double *d_S, const double *d_F,
+                                const double *d_Sigma_iw, double *d_G_iw) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_S || !d_F || !d_G_iw) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_dyson: NULL pointer");
+  if (!std::isfinite(mu)) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_dyson: mu not finite");
+  return launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw);
+}
+
+extern "C" gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_moments, double *d_P) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_G_iw || !d_moments || !d_P) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_density: NULL pointer");
+  double *coef = slot(ctx, SL_COEF);
+  gf2_status st = gf2_pole_coefficients(ctx, d_moments, coef);
+  if (st != GF2_OK) return st;
+  return launch_density(ctx, d_G_iw, coef, d_P);
+}
+
+extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
+                                    const double *d_Sigma_iw, const double *d_sig12, double n_elec,
+                                    double tol, int max_iter, double *mu_inout, double *d_G_iw,
+                                    double *d_P, int *n_eval) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_S || !d_F || !mu_inout || !d_G_iw || !d_P)
+    return gf2_fail(ctx, GF2_ERR_ARG, "gf2_mu_search: NULL pointer");
+  if (!(tol > 0.0) || max_iter < 1 || !std::isfinite(*mu_inout) || !(n_elec > 0.0) ||
+      !(n_elec < 2.0 * ctx->N))
+    return gf2_fail(ctx, GF2_ERR_ARG, "gf2_mu_search: bad tol, max_iter, mu or n_elec");
+  gf2_status st = build_moment_basis(ctx, d_S, d_F, d_sig12);
+  if (st != GF2_OK) return st;
+  double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
+  int evals = 0;
+  auto count = [&](double mu, double *out) -> gf2_status {
+    gf2_status s;
+    if ((s = launch_moments(ctx, mu, mom)) != GF2_OK) return s;
+    if ((s = gf2_pole_coefficients(ctx, mom, coef)) != GF2_OK) return s;
+    if ((s = launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw)) != GF2_OK) return s;
+    if ((s = launch_density(ctx, d_G_iw, coef, d_P)) != GF2_OK) return s;
+    trace_kernel<<<1, 256, 0, ctx->stream>>>(ctx->N, d_P, d_S, cnt);
+    GF2_CK_LAUNCH(ctx, "trace_kernel");
+    GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, cnt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ++evals;
+    int flag = 0;
+    memcpy(&flag, ctx->h_pinned + 1, sizeof(int));
+    if (flag) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: vanishing Dyson pivot");
+    *out = ctx->h_pinned[0] - n_elec;
+    if (!std::isfinite(*out)) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: non-finite count");
+    return GF2_OK;
+  };
+  auto done = [&](double mu) {
+    *mu_inout = mu;
+    if (n_eval) *n_eval = evals;
+    return GF2_OK;
+  };
+  double mu0 = *mu_inout, f0;
+  if ((st = count(mu0, &f0)) != GF2_OK) return st;
+  if (fabs(f0) <= tol) return done(mu0);
+  // bracket: step outward, doubling
+  double lo, hi, flo, fhi, step = 0.05;
+  if (f0 < 0.0) {
+    lo = mu0; flo = f0; hi = mu0 + step;
+    for (;;) {
+      if (evals >= max_iter) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: no bracket");
+      if ((st = count(hi, &fhi)) != GF2_OK) return st;
+      if (fabs(fhi) <= tol) return done(hi);
+      if (fhi > 0.0) break;
+      lo = hi; flo = fhi; step *= 2.0; hi += step;
+    }
+  } else {
+    hi = mu0; fhi = f0; lo = mu0 - step;
+    for (;;) {
+      if (evals >= max_iter) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: no bracket");
+      if ((st = count(lo, &flo)) != GF2_OK) return st;
+      if (fabs(flo) <= tol) return done(lo);
+      if (flo < 0.0) break;
+      hi = lo; fhi = flo; step *= 2.0; lo -= step;
+    }
+  }
+  // Illinois false position, bisecting whenever the secant point is unusable
+  int side = 0;
+  double last = mu0;
+  while (evals < max_iter) {
+    double mu = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(mu > lo && mu < hi) || (hi - lo) < 1e-15 * std::max(1.0, fabs(mu))) mu = 0.5 * (lo + hi);
+    double f;
+    if ((st = count(mu, &f)) != GF2_OK) return st;
+    last = mu;
+    if (fabs(f) <= tol) return done(mu);
+    if (f < 0.0) {
+      lo = mu; flo = f;
+      if (side == -1) fhi *= 0.5;
+      side = -1;
+    } else {
+      hi = mu; fhi = f;
+      if (side == 1) flo *= 0.5;
+      side = 1;
+    }
+  }
+  *mu_inout = last;
+  if (n_eval) *n_eval = evals;
+  return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: tolerance not reached");
+}
+
+extern "C" gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_P, double *d_F) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_h || !d_P || !d_F) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: NULL pointer");
+  if (!ctx->have_integrals) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: gf2_set_integrals not called");
+  fock_kernel<<<ctx->N, ((ctx->N + 31) / 32) * 32, 0, ctx->stream>>>(ctx->N, d_h, ctx->d_v, d_P, d_F);
+  GF2_CK_LAUNCH(ctx, "fock_kernel");
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *d_F, const double *d_P,
+                                 const double *d_S, const double *d_G_iw, const double *d_Sigma_iw,
+                                 const double *d_sig12, double *e_one_body, double *e_two_body) {
+  if (!ctx) return GF2_ERR_ARG;
+  if (!d_h || !d_F || !d_P || !d_S || !d_G_iw || !d_Sigma_iw || !e_one_body || !e_two_body)
+    return gf2_fail(ctx, GF2_ERR_ARG, "gf2_energy: NULL pointer");
+  gf2_status st;
+  if (d_sig12 && (st = gf2_inverse_spd(ctx, d_S, slot(ctx, SL_SINV))) != GF2_OK) return st;
+  energy_partial_kernel<<<ctx->n_iw, 256, 0, ctx->stream>>>(
+      ctx->N, reinterpret_cast<const double2 *>(d_G_iw), reinterpret_cast<const double2 *>(d_Sigma_iw), ctx->d_red);
+  GF2_CK_LAUNCH(ctx, "energy_partial_kernel");
+  double *out = slot(ctx, SL_MISC);
+  energy_final_kernel<<<1, 256, 0, ctx->stream>>>(ctx->N, ctx->n_iw, ctx->beta, ctx->d_red, d_P, d_h, d_F,
+                                                  slot(ctx, SL_SINV), d_sig12, out);
+  GF2_CK_LAUNCH(ctx, "energy_final_kernel");
+  GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  *e_one_body = ctx->h_pinned[0];
+  *e_two_body = ctx->h_pinned[1];
+  return GF2_OK;
+}

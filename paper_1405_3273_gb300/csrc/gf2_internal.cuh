@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libgf2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/gf2.h"
+
+// Real pole (hartree) about which the four-moment tail is resummed:
+// T(z) = sum_r c_r (z - a)^-r with the moments G1..G4 of Eq. GF.
+#define GF2_TAIL_POLE 1.0
+#define GF2_MAX_N 112
+
+// slots of ctx->d_small, each N*N doubles
+enum {
+  GF2_SL_SINV = 0, GF2_SL_A1, GF2_SL_A2, GF2_SL_A3, GF2_SL_B1, GF2_SL_B2, GF2_SL_B3,
+  GF2_SL_T1, GF2_SL_TMP, GF2_SL_MOM = 9, GF2_SL_COEF = 13, GF2_SL_MISC = 17, GF2_SL_COUNT = 20
+};
+
+struct gf2_ctx {
+  int N = 0, n_tau = 0, n_iw = 0, M = 0, log2M = 0;
+  double beta = 0.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string last_error;
+
+  // integrals (FP64, owned copies)
+  double *d_v = nullptr;    // v[i][j][k][l] = (ij|kl)
+  double *d_Wt = nullptr;   // Wt[n][p][l][j] = W[l][p][n][j] = 2 v_lpnj - v_nplj
+  bool have_integrals = false;
+
+  // tensor-core operands (BF16 split planes), built by gf2_set_integrals
+  void *d_v_split = nullptr;    // [terms][N^4] bf16: v[i][m][q][k]
+  void *d_wt_split = nullptr;   // [terms][N^4] bf16: Wt4[j][l][n][p] = W[l][p][n][j]
+  int split_terms = 0;
+
+  // grid tables (built at create)
+  double2 *d_twiddle = nullptr;   // e^{-2 pi i k / M}, k < M/2
+  double2 *d_iw_pole = nullptr;   // [n_iw][4]: (i w_n - a)^-(r+1)
+  double *d_tau_pole = nullptr;   // [n_tau][4]: tau image of (z - a)^-(r+1)
+  double *d_pole_resum = nullptr; // [4]: sum_{n<n_iw} Re (i w_n - a)^-(r+1)
+  double2 *d_t2w_w = nullptr;     // [n_iw]: h W(theta_n), attenuation factor
+  double2 *d_t2w_corr = nullptr;  // [n_iw][8]: end corrections, nodes 0..3, M-3..M
+
+  // FP64 Sigma workspace (two ping-pong buffers of chunk * N^4 doubles)
+  double *d_ws = nullptr;
+  size_t ws_elems = 0;
+  int fp64_chunk = 0;
+
+  // tensor-core Sigma workspace
+  void *d_tc_ws = nullptr;
+  size_t tc_ws_bytes = 0;
+  int tc_chunk = 0;
+  int *d_err = nullptr;           // device error word (timeouts in tcgen05 kernels)
+
+  // small scratch
+  double *d_small = nullptr;      // Sinv, basis(7), coef(4), misc: 16 N^2
+  double *d_red = nullptr;        // reduction partials
+  size_t red_elems = 0;
+  double *h_pinned = nullptr;     // host-pinned scalars (8 doubles)
+};
+
+// ---- error helpers (host) ----
+gf2_status gf2_fail(gf2_ctx *ctx, gf2_status s, const std::string &msg);
+gf2_status gf2_cuda_fail(gf2_ctx *ctx, cudaError_t e, const char *what);
+
+#define GF2_CK(ctx, call)                                                  \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return gf2_cuda_fail((ctx), e_, #call);         \
+  } while (0)
+
+#define GF2_CK_LAUNCH(ctx, what)                                           \
+  do {                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                   \
+    if (e_ != cudaSuccess) return gf2_cuda_fail((ctx), e_, (what));        \
+  } while (0)
+
+// ---- FP64 strided batched GEMM: C = alpha * A B + beta_c * C ----
+struct Dgemm {
+  int M, N, K;
+  const double *A; long long a_rs, a_cs, a_b0, a_b1;
+  const double *B; long long b_rs, b_cs, b_b0, b_b1;
+  double *C;       long long c_rs, c_cs, c_b0, c_b1;
+  int nb0, nb1;
+  double alpha, beta_c;
+  int split_k;   // > 1: partial products added with atomics (C must hold beta_c*C already)
+};
+gf2_status gf2_dgemm(gf2_ctx *ctx, const Dgemm &g);
+
+// inverse of a real symmetric positive-definite matrix (Gauss-Jordan, one CTA)
+gf2_status gf2_inverse_spd(gf2_ctx *ctx, const double *d_A, double *d_Ainv);
+
+// ---- internal entry points between translation units ----
+gf2_status gf2_tables_build(gf2_ctx *ctx);
+gf2_status gf2_pole_coefficients(gf2_ctx *ctx, const double *d_moments, double *d_coef);
+gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out);
+gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out,
+                        int prec);
+gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx);
+
+// ---- small device helpers ----
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline double2 crecip(double2 a) {
+  double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}

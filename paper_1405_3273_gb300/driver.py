@@ -1,0 +1,137 @@
+"""The self-consistent GF2 loop (steps 1-3 of the paper's supplement) driven
+through the libgf2 C-ABI.  Every numerical step runs in the library's CUDA
+kernels; this module only sequences calls and moves a few scalars.
+
+State kept on the device per iteration: F, mu, G(i w), P, Sigma(tau),
+Sigma(i w) and the tail coefficients (Sig1, Sig2).
+"""
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import (GF2_PREC_BF16X3, GF2_PREC_FP64, Context, gf2_energy, gf2_fft_iw_to_tau,
+               gf2_fft_tau_to_iw, gf2_fock, gf2_mu_search, gf2_set_integrals, gf2_sigma_tau,
+               gf2_tail_moments)
+
+
+@dataclass
+class DeviceSystem:
+    S: torch.Tensor
+    h: torch.Tensor
+    v: torch.Tensor
+    F0: torch.Tensor
+    e_nuc: float
+    n_elec: int
+    beta: float
+    n_tau: int
+    n_iw: int
+    mu0: float
+
+    @property
+    def nbf(self):
+        return self.S.shape[0]
+
+
+def to_device(system, F_start, mu0, device="cuda"):
+    f = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+    return DeviceSystem(S=f(system.S), h=f(system.h), v=f(system.eri), F0=f(F_start),
+                        e_nuc=float(system.e_nuc), n_elec=int(system.n_elec), beta=float(system.beta),
+                        n_tau=int(system.n_tau), n_iw=int(system.n_iw), mu0=float(mu0))
+
+
+@dataclass
+class GF2Run:
+    ctx: Context
+    sys: DeviceSystem
+    prec: int = GF2_PREC_FP64
+    F: torch.Tensor = None
+    mu: float = 0.0
+    P: torch.Tensor = None
+    G_iw: torch.Tensor = None
+    G_tau: torch.Tensor = None
+    Sigma_tau: torch.Tensor = None
+    Sigma_iw: torch.Tensor = None
+    sig12: torch.Tensor = None
+    moments: torch.Tensor = None
+    energies: list = field(default_factory=list)
+    mu_evals: list = field(default_factory=list)
+
+
+def start(sys, prec=GF2_PREC_FP64):
+    n, nt, nw = sys.nbf, sys.n_tau, sys.n_iw
+    ctx = Context(n, nt, nw, sys.beta)
+    gf2_set_integrals(ctx.handle, sys.v)
+    dev = sys.S.device
+    run = GF2Run(ctx=ctx, sys=sys, prec=prec)
+    run.F = sys.F0.clone()
+    run.mu = sys.mu0
+    run.P = torch.zeros(n, n, dtype=torch.float64, device=dev)
+    run.G_iw = torch.zeros(nw, n, n, dtype=torch.complex128, device=dev)
+    run.G_tau = torch.zeros(nt, n, n, dtype=torch.float64, device=dev)
+    run.Sigma_tau = torch.zeros(nt, n, n, dtype=torch.float64, device=dev)
+    run.Sigma_iw = torch.zeros(nw, n, n, dtype=torch.complex128, device=dev)
+    run.sig12 = None
+    run.moments = torch.zeros(4, n, n, dtype=torch.float64, device=dev)
+    return run
+
+
+def inner_loop(run, tol=1e-10, max_iter=200, mu_tol=1e-10):
+    """Steps 2.a-2.b: mu search and Fock rebuild until F stops changing."""
+    s = run.sys
+    F_new = torch.empty_like(run.F)
+    for _ in range(max_iter):
+        run.mu, nev = gf2_mu_search(run.ctx.handle, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
+                                    run.G_iw, run.P, tol=mu_tol)
+        run.mu_evals.append(nev)
+        gf2_fock(run.ctx.handle, s.h, run.P, F_new)
+        diff = (F_new - run.F).abs().max().item()
+        run.F.copy_(F_new)
+        if diff < tol:
+            # G and P at the final F
+            run.mu, nev = gf2_mu_search(run.ctx.handle, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec,
+                                        run.mu, run.G_iw, run.P, tol=mu_tol)
+            run.mu_evals.append(nev)
+            return
+    raise RuntimeError("inner loop did not converge")
+
+
+def energy(run):
+    s = run.sys
+    e1, e2 = gf2_energy(run.ctx.handle, s.h, run.F, run.P, s.S, run.G_iw, run.Sigma_iw, run.sig12)
+    return s.e_nuc + e1 + e2, e1, e2
+
+
+def self_energy_step(run, damping=1.0):
+    """G(i w) -> G(tau) -> Sigma(tau) (optionally damped) -> Sigma(i w)."""
+    s = run.sys
+    gf2_tail_moments(run.ctx.handle, s.S, run.F, run.mu, run.sig12, run.moments)
+    gf2_fft_iw_to_tau(run.ctx.handle, run.G_iw, run.moments, run.G_tau)
+    if damping < 1.0 and run.sig12 is not None:
+        new = torch.empty_like(run.Sigma_tau)
+        gf2_sigma_tau(run.ctx.handle, run.G_tau, new, run.prec)
+        run.Sigma_tau.mul_(1.0 - damping).add_(new, alpha=damping)
+    else:
+        gf2_sigma_tau(run.ctx.handle, run.G_tau, run.Sigma_tau, run.prec)
+    if run.sig12 is None:
+        run.sig12 = torch.empty(2, s.nbf, s.nbf, dtype=torch.float64, device=s.S.device)
+    gf2_fft_tau_to_iw(run.ctx.handle, run.Sigma_tau, run.Sigma_iw, run.sig12)
+
+
+def run_gf2(sys, prec=GF2_PREC_FP64, max_outer=30, e_tol=1e-8, damping=1.0, inner_tol=1e-10, callback=None):
+    run = start(sys, prec)
+    inner_loop(run, inner_tol)
+    run.energies.append(energy(run))
+    for _ in range(max_outer):
+        self_energy_step(run, damping)
+        inner_loop(run, inner_tol)
+        run.energies.append(energy(run))
+        if callback is not None:
+            callback(run)
+        if abs(run.energies[-1][0] - run.energies[-2][0]) < e_tol:
+            break
+    return run
+
+
+__all__ = ["DeviceSystem", "to_device", "GF2Run", "start", "inner_loop", "energy", "self_energy_step",
+           "run_gf2", "GF2_PREC_FP64", "GF2_PREC_BF16X3"]

@@ -1,0 +1,62 @@
+"""Host-side checks of the C-ABI library (no GPU needed, no compute calls)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gf2.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:gf2_status|const char \*)\s*(gf2_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def library():
+    from paper_1405_3273_gb300 import LIB_PATH, build
+    if not os.path.exists(LIB_PATH):
+        build.build()
+    return ctypes.CDLL(LIB_PATH)
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_functions()
+    for required in ["gf2_sigma_tau", "gf2_fft_tau_to_iw", "gf2_fft_iw_to_tau", "gf2_dyson",
+                     "gf2_mu_search", "gf2_energy", "gf2_create", "gf2_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(library):
+    for name in declared_functions():
+        assert hasattr(library, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_1405_3273_gb300 as g
+    assert sorted(g.exported_symbols()) == declared_functions()
+    for name in declared_functions():
+        assert callable(getattr(g, name, None)) or name in ("gf2_status_string", "gf2_last_error")
+
+
+def test_status_strings_without_gpu(library):
+    library.gf2_status_string.restype = ctypes.c_char_p
+    library.gf2_status_string.argtypes = [ctypes.c_int]
+    assert library.gf2_status_string(0) == b"ok"
+    assert library.gf2_status_string(1) == b"invalid argument"
+
+
+def test_create_rejects_bad_sizes_before_touching_the_device(library):
+    f = library.gf2_create
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_double, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    assert f(ctypes.byref(h), 10, 100, 64, 10.0, None) == 1       # M = 99 not a power of two
+    assert f(ctypes.byref(h), 0, 129, 64, 10.0, None) == 1        # N = 0
+    assert f(ctypes.byref(h), 10, 129, 64, -1.0, None) == 1       # beta < 0
+    assert f(None, 10, 129, 64, 10.0, None) == 1                  # NULL out
+    assert h.value is None

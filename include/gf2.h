@@ -83,6 +83,16 @@ const char *gf2_last_error(const gf2_ctx *ctx);
  * split copies for the tensor-core path. */
 gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v);
 
+/* Give the context the overlap S [N][N] (symmetric positive definite).  The
+ * split-precision Sigma path then evaluates Eq. Sigma in the symmetrically
+ * orthogonalised basis (G' = S^1/2 G S^1/2, v' = (S^-1/2)^{x4} v, returned as
+ * Sigma = S^1/2 Sigma' S^1/2), where the entries of G' are bounded by one and
+ * FP32 accumulation loses no digits to the cancellations that an ill-
+ * conditioned S produces in the AO basis.  Mathematically the same Sigma (the
+ * equation is covariant); the FP64 path is unaffected.  Optional; may be
+ * called before or after gf2_set_integrals. */
+gf2_status gf2_set_overlap(gf2_ctx *ctx, const double *d_S);
+
 /* Eq. Sigma (the paper's second-order self-energy):
  *   Sigma_ij(tau) = - sum_klmnpq G_kl(tau) G_mn(tau) G_pq(-tau) v_imqk (2 v_lpnj - v_nplj)
  * with G(-tau_k) = -G(tau_{M-k}).  d_G_tau [n_tau][N][N] in, d_Sigma_tau
@@ -159,6 +169,30 @@ gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_P, double *
 gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *d_F, const double *d_P,
                       const double *d_S, const double *d_G_iw, const double *d_Sigma_iw,
                       const double *d_sig12, double *e_one_body, double *e_two_body);
+
+/* Convergence aids of the self-consistent loop.  The supplement damps P in
+ * the inner loop and Sigma(tau) in the outer loop (amounts unstated); both
+ * are linear combinations of device arrays.  The inner loop also uses Pulay
+ * extrapolation of F (no counterpart in the paper), which needs the Gram
+ * matrix of the residuals.
+ *   gf2_combine: d_out[e] = sum_{k<n} coef[k] d_src[k][e], e < count
+ *                (coef: host array of n doubles; d_src: host array of n device
+ *                pointers; 1 <= n <= 16; d_out may alias one source).
+ *   gf2_gram:    gram_out[a*n + b] = sum_e d_vecs[a][e] d_vecs[b][e]
+ *                (gram_out: host array of n*n doubles).  Synchronizes. */
+gf2_status gf2_combine(gf2_ctx *ctx, int n, const double *coef, const double *const *d_src,
+                       long long count, double *d_out);
+gf2_status gf2_gram(gf2_ctx *ctx, int n, const double *const *d_vecs, long long count, double *gram_out);
+
+/* Tracing (no counterpart in the paper).  gf2_profile(ctx, 1) clears the
+ * counters and starts timing every kernel launch of the context with CUDA
+ * events on its stream (0 stops; launches are counted either way).
+ * gf2_profile_report writes one line "name launches total_ms" per kernel kind
+ * into buf (NUL-terminated; GF2_ERR_ARG if buflen is too small) and the
+ * number of kernel launches since the last gf2_profile call into *launches
+ * (may be NULL).  The report synchronizes on the recorded events. */
+gf2_status gf2_profile(gf2_ctx *ctx, int enable);
+gf2_status gf2_profile_report(gf2_ctx *ctx, char *buf, int buflen, long long *launches);
 
 #ifdef __cplusplus
 }

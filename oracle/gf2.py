@@ -11,6 +11,7 @@
 Optional damping (the supplement damps P in the inner loop and Sigma(tau) in
 the outer loop without stating amounts): P <- a_P P_new + (1-a_P) P_old and
 Sigma <- a_S Sigma_new + (1-a_S) Sigma_old, both 1 (no damping) by default.
+The inner loop extrapolates F by Pulay's DIIS (see ``inner_loop``).
 """
 
 from dataclasses import dataclass, field
@@ -37,22 +38,55 @@ class GF2State:
     energies: list = field(default_factory=list)
 
 
-def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-10, max_iter=200,
-               p_damping=1.0):
-    """Steps 2.a-2.b: alternate the mu search and the Fock rebuild to self-consistency."""
+def _diis_coefficients(gram):
+    """Pulay weights: minimise |sum c_a R_a| subject to sum c_a = 1."""
+    m = gram.shape[0]
+    B = np.zeros((m + 1, m + 1))
+    B[:m, :m] = gram
+    B[m, :m] = B[:m, m] = -1.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = -1.0
+    return np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
+
+
+def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-8, max_iter=200,
+               p_damping=1.0, diis=8):
+    """Steps 2.a-2.b: alternate the mu search and the Fock rebuild to self-consistency.
+
+    Converged when the Fock residual R = F(P(F)) - F has Frobenius norm below
+    ``tol`` (the mu search stops anywhere within 1e-10 electrons, which leaves
+    a noise floor near 1e-9 in R).  With ``diis`` > 0 the next F is the Pulay
+    extrapolation of the
+    last ``diis`` rebuilt matrices (the plain fixed-point map is unstable for
+    some lattices at finite temperature); G, P and mu are then re-evaluated at
+    the converged F.
+    """
     S, h, v = system.S, system.h, system.eri
     P_old = None
+    hist_F, hist_R = [], []
     for _ in range(max_iter):
         mu, G, P, _ = dy.mu_search(S, F, Sigma_iw, sig1, sig2, system.n_elec, beta, n_iw)
         if P_old is not None and p_damping < 1.0:
             P = p_damping * P + (1.0 - p_damping) * P_old
-        F_new = fock(h, v, P)
-        converged = np.abs(F_new - F).max() < tol
-        F, P_old = F_new, P
-        if converged:
-            # G, P and mu evaluated at the converged F
+        P_old = P
+        F_out = fock(h, v, P)
+        R = F_out - F
+        if np.sqrt(np.sum(R * R)) < tol:
+            F = F_out
             mu, G, P, _ = dy.mu_search(S, F, Sigma_iw, sig1, sig2, system.n_elec, beta, n_iw)
             return F, mu, G, P
+        if diis > 0:
+            hist_F.append(F_out)
+            hist_R.append(R)
+            hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
+            if len(hist_F) > 1:
+                gram = np.array([[np.sum(a * b) for b in hist_R] for a in hist_R])
+                c = _diis_coefficients(gram)
+                F = sum(ci * fi for ci, fi in zip(c, hist_F))
+            else:
+                F = F_out
+        else:
+            F = F_out
     raise RuntimeError("inner loop did not converge")
 
 
@@ -73,11 +107,11 @@ def self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn=None):
 
 
 def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damping=1.0,
-        p_damping=1.0, inner_tol=1e-10, sigma_fn=None, callback=None):
+        p_damping=1.0, inner_tol=1e-8, sigma_fn=None, callback=None, diis=8):
     """Full GF2; returns the final GF2State (energies[] holds (E, E1, E2) per iteration)."""
     n = system.nbf
     F, mu, G, P = inner_loop(system, F_start, None, None, None, beta, n_iw, inner_tol,
-                             p_damping=p_damping)
+                             p_damping=p_damping, diis=diis)
     state = GF2State(F=F, mu=mu, P=P, G_iw=G, sig1=np.zeros((n, n)), sig2=np.zeros((n, n)))
     state.energies.append(energy(system, state, beta))
     for _ in range(max_outer):
@@ -89,7 +123,7 @@ def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damp
         state.sig1, state.sig2 = sigma_expansion(Sig_tau, beta)
         state.F, state.mu, state.G_iw, state.P = inner_loop(
             system, state.F, state.Sigma_iw, state.sig1, state.sig2, beta, n_iw, inner_tol,
-            p_damping=p_damping)
+            p_damping=p_damping, diis=diis)
         state.energies.append(energy(system, state, beta))
         if callback is not None:
             callback(state)

@@ -37,6 +37,7 @@ _SIGS = {
     "gf2_status_string": [_I],
     "gf2_last_error": [_P],
     "gf2_set_integrals": [_P, _P],
+    "gf2_set_overlap": [_P, _P],
     "gf2_sigma_tau": [_P, _P, _P, _I],
     "gf2_sigma_tau_points": [_P, _P, _I, _I, _P, _I],
     "gf2_tail_moments": [_P, _P, _P, _D, _P, _P],
@@ -47,6 +48,10 @@ _SIGS = {
     "gf2_mu_search": [_P, _P, _P, _P, _P, _D, _D, _I, ctypes.POINTER(_D), _P, _P, ctypes.POINTER(_I)],
     "gf2_fock": [_P, _P, _P, _P],
     "gf2_energy": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "gf2_combine": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.c_longlong, _P],
+    "gf2_gram": [_P, _I, ctypes.POINTER(_P), ctypes.c_longlong, ctypes.POINTER(_D)],
+    "gf2_profile": [_P, _I],
+    "gf2_profile_report": [_P, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong)],
 }
 
 
@@ -121,6 +126,10 @@ def gf2_set_integrals(ctx, v):
     _check(lib().gf2_set_integrals(ctx, _ptr(v, _F64)), ctx)
 
 
+def gf2_set_overlap(ctx, S):
+    _check(lib().gf2_set_overlap(ctx, _ptr(S, _F64)), ctx)
+
+
 def gf2_sigma_tau(ctx, G_tau, Sigma_tau, prec=GF2_PREC_FP64):
     _check(lib().gf2_sigma_tau(ctx, _ptr(G_tau, _F64), _ptr(Sigma_tau, _F64), int(prec)), ctx)
 
@@ -172,6 +181,37 @@ def gf2_energy(ctx, h, F, P, S, G_iw, Sigma_iw, sig12):
                             _ptr(G_iw, _C128), _ptr(Sigma_iw, _C128), _ptr(sig12, _F64),
                             ctypes.byref(e1), ctypes.byref(e2)), ctx)
     return e1.value, e2.value
+
+
+def gf2_combine(ctx, coefs, srcs, out):
+    n = len(coefs)
+    c = (ctypes.c_double * n)(*[float(x) for x in coefs])
+    p = (ctypes.c_void_p * n)(*[_ptr(t, _F64) for t in srcs])
+    _check(lib().gf2_combine(ctx, n, c, p, out.numel(), _ptr(out, _F64)), ctx)
+
+
+def gf2_gram(ctx, vecs):
+    n = len(vecs)
+    p = (ctypes.c_void_p * n)(*[_ptr(t, _F64) for t in vecs])
+    out = (ctypes.c_double * (n * n))()
+    _check(lib().gf2_gram(ctx, n, p, vecs[0].numel(), out), ctx)
+    return [[out[a * n + b] for b in range(n)] for a in range(n)]
+
+
+def gf2_profile(ctx, enable=True):
+    _check(lib().gf2_profile(ctx, 1 if enable else 0), ctx)
+
+
+def gf2_profile_report(ctx):
+    """{kernel: (launches, total_ms)} since the last gf2_profile call, and the launch count."""
+    buf = ctypes.create_string_buffer(1 << 14)
+    n = ctypes.c_longlong(0)
+    _check(lib().gf2_profile_report(ctx, buf, len(buf), ctypes.byref(n)), ctx)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out, n.value
 
 
 class Context:

@@ -119,7 +119,7 @@ gf2_status gf2_dgemm(gf2_ctx *ctx, const Dgemm &g) {
   const int tiles_m = (g.M + TM - 1) / TM, tiles_n = (g.N + TN - 1) / TN;
   const int ks = g.split_k > 1 ? g.split_k : 1;
   dim3 grid(tiles_m * tiles_n * ks, g.nb0, g.nb1);
-  dgemm_kernel<<<grid, 256, 0, ctx->stream>>>(g, tiles_m, tiles_n);
+  GF2_PROF(ctx, GF2_K_DGEMM, (dgemm_kernel<<<grid, 256, 0, ctx->stream>>>(g, tiles_m, tiles_n)));
   GF2_CK_LAUNCH(ctx, "dgemm_kernel");
   return GF2_OK;
 }

@@ -290,9 +290,10 @@ gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *
   const size_t smem = sizeof(double2) * ((size_t)N * N + 2 * N);
   GF2_CK(ctx, cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-  dyson_kernel<<<ctx->n_iw, 256, smem, ctx->stream>>>(N, ctx->beta, mu, S, F,
-                                                       reinterpret_cast<const double2 *>(Sig),
-                                                       reinterpret_cast<double2 *>(G), ctx->d_err);
+  GF2_PROF(ctx, GF2_K_DYSON,
+           (dyson_kernel<<<ctx->n_iw, 256, smem, ctx->stream>>>(N, ctx->beta, mu, S, F,
+                                                                reinterpret_cast<const double2 *>(Sig),
+                                                                reinterpret_cast<double2 *>(G), ctx->d_err)));
   GF2_CK_LAUNCH(ctx, "dyson_kernel");
   return GF2_OK;
 }
@@ -302,8 +303,9 @@ gf2_status launch_density(gf2_ctx *ctx, const double *G, const double *coef, dou
   const int chunk = 256;
   const int nchunks = (ctx->n_iw + chunk - 1) / chunk;
   dim3 grid((N2 + 127) / 128, nchunks);
-  density_partial_kernel<<<grid, 128, 0, ctx->stream>>>(N2, ctx->n_iw, chunk,
-                                                         reinterpret_cast<const double2 *>(G), ctx->d_red);
+  GF2_PROF(ctx, GF2_K_DENSITY,
+           (density_partial_kernel<<<grid, 128, 0, ctx->stream>>>(N2, ctx->n_iw, chunk,
+                                                                  reinterpret_cast<const double2 *>(G), ctx->d_red)));
   GF2_CK_LAUNCH(ctx, "density_partial_kernel");
   density_final_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(
       N2, nchunks, ctx->beta, ctx->d_red, coef, ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M, P);
@@ -437,7 +439,8 @@ extern "C" gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_
   if (!ctx) return GF2_ERR_ARG;
   if (!d_h || !d_P || !d_F) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: NULL pointer");
   if (!ctx->have_integrals) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: gf2_set_integrals not called");
-  fock_kernel<<<ctx->N, ((ctx->N + 31) / 32) * 32, 0, ctx->stream>>>(ctx->N, d_h, ctx->d_v, d_P, d_F);
+  GF2_PROF(ctx, GF2_K_FOCK,
+           (fock_kernel<<<ctx->N, ((ctx->N + 31) / 32) * 32, 0, ctx->stream>>>(ctx->N, d_h, ctx->d_v, d_P, d_F)));
   GF2_CK_LAUNCH(ctx, "fock_kernel");
   return GF2_OK;
 }
@@ -450,8 +453,10 @@ extern "C" gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *
     return gf2_fail(ctx, GF2_ERR_ARG, "gf2_energy: NULL pointer");
   gf2_status st;
   if (d_sig12 && (st = gf2_inverse_spd(ctx, d_S, slot(ctx, SL_SINV))) != GF2_OK) return st;
-  energy_partial_kernel<<<ctx->n_iw, 256, 0, ctx->stream>>>(
-      ctx->N, reinterpret_cast<const double2 *>(d_G_iw), reinterpret_cast<const double2 *>(d_Sigma_iw), ctx->d_red);
+  GF2_PROF(ctx, GF2_K_ENERGY,
+           (energy_partial_kernel<<<ctx->n_iw, 256, 0, ctx->stream>>>(
+               ctx->N, reinterpret_cast<const double2 *>(d_G_iw), reinterpret_cast<const double2 *>(d_Sigma_iw),
+               ctx->d_red)));
   GF2_CK_LAUNCH(ctx, "energy_partial_kernel");
   double *out = slot(ctx, SL_MISC);
   energy_final_kernel<<<1, 256, 0, ctx->stream>>>(ctx->N, ctx->n_iw, ctx->beta, ctx->d_red, d_P, d_h, d_F,

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
 #include <new>
 
 #include "gf2_internal.cuh"
@@ -36,16 +37,92 @@ __global__ void build_wt_kernel(int N, const double *__restrict__ v, double *__r
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+const char *kKernelNames[GF2_K_COUNT] = {"sigma_sandwich", "sigma_xform", "sigma_contract", "sigma_split_g",
+                                         "dgemm_fp64", "dyson_inverse", "density_reduce", "fft_iw_to_tau",
+                                         "fft_tau_to_iw", "fock_build", "energy_reduce", "small"};
+
+void prof_drain(gf2_ctx *c) {
+  for (auto &r : c->prof_recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.id] += ms;
+      c->prof_n[r.id] += 1;
+    }
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+}
+
 void free_all(gf2_ctx *c) {
-  void *ptrs[] = {c->d_v, c->d_Wt, c->d_v_split, c->d_wt_split, c->d_twiddle, c->d_iw_pole,
+  for (auto &r : c->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  c->prof_recs.clear();
+  c->prof_pool.clear();
+  void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_twiddle, c->d_iw_pole,
                   c->d_tau_pole, c->d_pole_resum, c->d_t2w_w, c->d_t2w_corr, c->d_ws,
-                  c->d_tc_ws, c->d_err, c->d_small, c->d_red};
+                  c->d_err, c->d_small, c->d_red};
+  gf2_tc_release(c);
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
 }
 
 }  // namespace
+
+int gf2_prof_begin(gf2_ctx *ctx, int id) {
+  if (!ctx->prof_on) return -1;
+  if (ctx->prof_recs.size() > 4096) prof_drain(ctx);
+  gf2_prof_rec r;
+  r.id = id;
+  for (cudaEvent_t *e : {&r.a, &r.b}) {
+    if (!ctx->prof_pool.empty()) {
+      *e = ctx->prof_pool.back();
+      ctx->prof_pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return -1;
+    }
+  }
+  cudaEventRecord(r.a, ctx->stream);
+  ctx->prof_recs.push_back(r);
+  return (int)ctx->prof_recs.size() - 1;
+}
+
+void gf2_prof_end(gf2_ctx *ctx, int rec) {
+  if (rec < 0 || rec >= (int)ctx->prof_recs.size()) return;
+  cudaEventRecord(ctx->prof_recs[rec].b, ctx->stream);
+}
+
+extern "C" gf2_status gf2_profile(gf2_ctx *ctx, int enable) {
+  if (!ctx) return GF2_ERR_ARG;
+  prof_drain(ctx);
+  for (int k = 0; k < GF2_K_COUNT; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
+  ctx->prof_on = enable != 0;
+  ctx->launches = 0;
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_profile_report(gf2_ctx *ctx, char *buf, int buflen, long long *launches) {
+  if (!ctx || !buf || buflen < 1) return GF2_ERR_ARG;
+  prof_drain(ctx);
+  std::string out;
+  for (int k = 0; k < GF2_K_COUNT; ++k) {
+    if (!ctx->prof_n[k]) continue;
+    char line[128];
+    snprintf(line, sizeof line, "%s %lld %.6f\n", kKernelNames[k], ctx->prof_n[k], ctx->prof_ms[k]);
+    out += line;
+  }
+  if ((int)out.size() >= buflen) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_profile_report: buffer too small");
+  memcpy(buf, out.c_str(), out.size() + 1);
+  if (launches) *launches = ctx->launches;
+  return GF2_OK;
+}
 
 extern "C" const char *gf2_status_string(gf2_status s) {
   switch (s) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/gf2.h"
 
@@ -18,6 +19,17 @@ enum {
   GF2_SL_T1, GF2_SL_TMP, GF2_SL_MOM = 9, GF2_SL_COEF = 13, GF2_SL_MISC = 17, GF2_SL_COUNT = 20
 };
 
+// kernels timed by the optional per-launch profiler (gf2_profile)
+enum gf2_kernel_id {
+  GF2_K_SANDWICH = 0, GF2_K_XFORM, GF2_K_CONTRACT, GF2_K_SPLIT, GF2_K_DGEMM, GF2_K_DYSON,
+  GF2_K_DENSITY, GF2_K_IW2TAU, GF2_K_TAU2IW, GF2_K_FOCK, GF2_K_ENERGY, GF2_K_SMALL, GF2_K_COUNT
+};
+
+struct gf2_prof_rec {
+  int id;
+  cudaEvent_t a, b;
+};
+
 struct gf2_ctx {
   int N = 0, n_tau = 0, n_iw = 0, M = 0, log2M = 0;
   double beta = 0.0;
@@ -28,6 +40,8 @@ struct gf2_ctx {
 
   // integrals (FP64, owned copies)
   double *d_v = nullptr;    // v[i][j][k][l] = (ij|kl)
+  double *d_Shalf = nullptr;   // S^{1/2} and S^{-1/2} (gf2_set_overlap), [2][N][N]
+  double *d_orth_ws = nullptr; // orthogonal-basis G(tau), Sigma, scratch for the split path
   double *d_Wt = nullptr;   // Wt[n][p][l][j] = W[l][p][n][j] = 2 v_lpnj - v_nplj
   bool have_integrals = false;
 
@@ -49,7 +63,7 @@ struct gf2_ctx {
   size_t ws_elems = 0;
   int fp64_chunk = 0;
 
-  // tensor-core Sigma workspace
+  // tensor-core Sigma workspace (host-side state owning device buffers)
   void *d_tc_ws = nullptr;
   size_t tc_ws_bytes = 0;
   int tc_chunk = 0;
@@ -60,7 +74,19 @@ struct gf2_ctx {
   double *d_red = nullptr;        // reduction partials
   size_t red_elems = 0;
   double *h_pinned = nullptr;     // host-pinned scalars (8 doubles)
+
+  // launch accounting and the optional event profiler
+  long long launches = 0;
+  bool prof_on = false;
+  std::vector<gf2_prof_rec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[GF2_K_COUNT] = {};
+  long long prof_n[GF2_K_COUNT] = {};
 };
+
+// profiler hooks: begin returns a record index (or -1 when off)
+int gf2_prof_begin(gf2_ctx *ctx, int kernel_id);
+void gf2_prof_end(gf2_ctx *ctx, int rec);
 
 // ---- error helpers (host) ----
 gf2_status gf2_fail(gf2_ctx *ctx, gf2_status s, const std::string &msg);
@@ -74,8 +100,17 @@ gf2_status gf2_cuda_fail(gf2_ctx *ctx, cudaError_t e, const char *what);
 
 #define GF2_CK_LAUNCH(ctx, what)                                           \
   do {                                                                     \
+    ++(ctx)->launches;                                                     \
     cudaError_t e_ = cudaGetLastError();                                   \
     if (e_ != cudaSuccess) return gf2_cuda_fail((ctx), e_, (what));        \
+  } while (0)
+
+// time one launch statement under the profiler
+#define GF2_PROF(ctx, id, stmt)                                            \
+  do {                                                                     \
+    int r_ = gf2_prof_begin((ctx), (id));                                  \
+    stmt;                                                                  \
+    gf2_prof_end((ctx), r_);                                               \
   } while (0)
 
 // ---- FP64 strided batched GEMM: C = alpha * A B + beta_c * C ----
@@ -100,6 +135,10 @@ gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G_tau, int k0, int count
 gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out,
                         int prec);
 gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx);
+void gf2_tc_release(gf2_ctx *ctx);
+gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int count, double **d_Gorth);
+gf2_status gf2_orth_sigma_to_ao(gf2_ctx *ctx, const double *d_Sig_orth, int count, double *d_out);
+gf2_status gf2_orth_transform_v(gf2_ctx *ctx, double *d_vorth);
 
 // ---- small device helpers ----
 __host__ __device__ inline double2 cmul(double2 a, double2 b) {

@@ -1,9 +1,929 @@
-// Tensor-core (tcgen05) split-precision Sigma path -- placeholder until the
-// kernels land; reports GF2_ERR_UNSUPPORTED.
+// Eq. Sigma on the sm_103a tensor cores (tcgen05 + TMEM, TMA-fed), with every
+// operand split into T BF16 terms and the products sum_{a+b<T} x_a y_b
+// accumulated in FP32 (T = 2: three products, T = 3: six).
+//
+// The basis is padded to NP = 64 (zero rows and columns contribute nothing).
+// Per chunk of C time points three kernels run back to back:
+//
+//  sandwich   stages 1+2 fused.  Unit (tau pair, i, q pair): the v tile
+//             V[(m,q), k] (128 x 64) is loaded once and used for both time
+//             points.  MMA1  D1[(m,q), l]   = sum_k V[(m,q),k] G[k,l]
+//             (TMEM) -> split by four epilogue warps into an MN-major smem
+//             operand A2[(q,l), m] -> MMA2  D2[(q,l), n] = sum_m A2 G[m,n]
+//             -> four more warps split and store T2[tau][i][q][l][n].
+//  xform      stage 3.  D3[(l,n), p] = sum_q T2[tau][i][q][(l,n)] Gbar[p,q]
+//             with T2 read MN-major straight from HBM by TMA;
+//             stores T3[tau][i][l][n][p].
+//  contract   stage 4.  Sigma[(tau,i), j] -= sum_K T3[(tau,i), K] Wt4[j, K],
+//             K = (l,n,p) of length NP^3, rows = two time points x 64 i.
+//             Split over K in slices of NP^2 (FP32 accumulation in TMEM per
+//             slice) and reduced into the FP64 output with atomics.
+//
+// All three are persistent, warp-specialised: one TMA producer thread, one
+// MMA-issuing thread, and epilogue warpgroups that own the TMEM lane quarters
+// (warp w reads lanes 32*(w%4) .. +31).  Waits are bounded; a timeout raises
+// the context error word and the kernel drains and exits.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include <cudaTypedefs.h>
+
 #include "gf2_internal.cuh"
+#include "tc_ptx.cuh"
 
-gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) { (void)ctx; return GF2_ERR_UNSUPPORTED; }
+namespace {
 
-gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *, int, int, double *, int) {
-  return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "tensor-core path not built");
+constexpr int NP = 64;
+constexpr int TMAX = 3;
+constexpr uint32_t TILE128 = 128 * NP * 2;  // 16 KB: 128 rows x 64 bf16
+constexpr uint32_t TILE64 = 64 * NP * 2;    //  8 KB: 64 rows x 64 bf16
+constexpr uint32_t kIdescKK = tc::idesc_bf16(128, 64, 0, 0);
+constexpr uint32_t kIdescMK = tc::idesc_bf16(128, 64, 1, 0);
+constexpr int kErrTimeout = 1;
+constexpr int kContractGroup = 2;  // 64-wide K steps per FP32 group in stage 4
+
+// product list (a, b) with a + b < T, smallest terms first
+template <int T>
+struct Products;
+template <>
+struct Products<2> {
+  static constexpr int n = 3;
+  __device__ static int a(int k) { return k == 0 ? 1 : 0; }
+  __device__ static int b(int k) { return k == 1 ? 1 : 0; }
+};
+template <>
+struct Products<3> {
+  static constexpr int n = 6;
+  __device__ static int a(int k) { const int t[6] = {2, 1, 0, 1, 0, 0}; return t[k]; }
+  __device__ static int b(int k) { const int t[6] = {0, 1, 2, 0, 1, 0}; return t[k]; }
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+  return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
+  *abort = 1;
+  atomicExch(err, kErrTimeout);
+}
+
+// write 64 consecutive fp32 values, split into T bf16 terms, as one 128-byte
+// row per term: dst[t * plane + 0..63]
+template <int T>
+__device__ __forceinline__ void store_row_split(__nv_bfloat16 *dst, size_t plane, const float *v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    __nv_bfloat16 p[8][T];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) tc::split_f32<T>(v[8 * c + e], p[e]);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      uint4 w;
+      w.x = tc::pack2(p[0][t], p[1][t]);
+      w.y = tc::pack2(p[2][t], p[3][t]);
+      w.z = tc::pack2(p[4][t], p[5][t]);
+      w.w = tc::pack2(p[6][t], p[7][t]);
+      *reinterpret_cast<uint4 *>(dst + t * plane + 8 * c) = w;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// splitting of the FP64 inputs
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_f64(double x, __nv_bfloat16 *p) {
+  double r = x;
+#pragma unroll
+  for (int t = 0; t < TMAX; ++t) {
+    p[t] = __double2bfloat16(r);
+    r -= (double)__bfloat162float(p[t]);
+  }
+}
+
+// Vs[t][i][m][q][k] = split_t v[i][m][q][k]  (zero outside N)
+__global__ void split_v_kernel(int N, const double *__restrict__ v, __nv_bfloat16 *__restrict__ Vs) {
+  const size_t plane = (size_t)NP * NP * NP * NP;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = idx % NP, q = (idx / NP) % NP, m = (idx / (NP * NP)) % NP, i = idx / (NP * NP * NP);
+    double x = 0.0;
+    if (i < N && m < N && q < N && k < N)
+      x = v[(((size_t)i * N + m) * N + q) * N + k];
+    __nv_bfloat16 p[TMAX];
+    split_f64(x, p);
+    for (int t = 0; t < TMAX; ++t) Vs[t * plane + idx] = p[t];
+  }
+}
+
+// Ws[t][j][l][n][p] = split_t W[l][p][n][j],  W_lpnj = 2 v_lpnj - v_nplj
+__global__ void split_w_kernel(int N, const double *__restrict__ v, __nv_bfloat16 *__restrict__ Ws) {
+  const size_t plane = (size_t)NP * NP * NP * NP;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int p = idx % NP, n = (idx / NP) % NP, l = (idx / (NP * NP)) % NP, j = idx / (NP * NP * NP);
+    double x = 0.0;
+    if (j < N && l < N && n < N && p < N) {
+      const double a = v[(((size_t)l * N + p) * N + n) * N + j];
+      const double b = v[(((size_t)n * N + p) * N + l) * N + j];
+      x = 2.0 * a - b;
+    }
+    __nv_bfloat16 p3[TMAX];
+    split_f64(x, p3);
+    for (int t = 0; t < TMAX; ++t) Ws[t * plane + idx] = p3[t];
+  }
+}
+
+// Gs[set][t][c][r][s]: set 0 = G(tau)^T (GT[l][k] = G[k][l]),
+//                      set 1 = Gbar = G(-tau) = -G(tau_{M-k}) (Gbar[p][q]).
+__global__ void split_g_kernel(int N, int M, int k0, int count, int C, const double *__restrict__ G,
+                               __nv_bfloat16 *__restrict__ Gs) {
+  const int c = blockIdx.x, set = blockIdx.y;
+  const size_t plane = (size_t)C * NP * NP;
+  for (int e = threadIdx.x; e < NP * NP; e += blockDim.x) {
+    const int r = e / NP, s = e % NP;
+    double x = 0.0;
+    if (c < count && r < N && s < N) {
+      const int k = k0 + c;
+      if (set == 0) x = G[(size_t)k * N * N + (size_t)s * N + r];
+      else x = -G[(size_t)(M - k) * N * N + (size_t)r * N + s];
+    }
+    __nv_bfloat16 p[TMAX];
+    split_f64(x, p);
+    for (int t = 0; t < TMAX; ++t) Gs[(size_t)(set * TMAX + t) * plane + (size_t)c * NP * NP + e] = p[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage 3: T3[c][i][l][n][p] = sum_q Gbar_c[p][q] T2[c][i][q][l][n]
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(192, 1)
+    xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
+                 __nv_bfloat16 *__restrict__ t3, int C, int n_units, int *err) {
+  constexpr int S = (T == 2) ? 4 : 3;
+  constexpr uint32_t A_STAGE = T * TILE128, B_SET = T * TILE64;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *sA = smem;
+  uint8_t *sB = sA + S * A_STAGE;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * B_SET);
+  uint64_t *a_full = bar, *a_empty = bar + S, *b_full = bar + 2 * S, *b_empty = bar + 2 * S + 2;
+  uint64_t *d_full = bar + 2 * S + 4, *d_empty = bar + 2 * S + 6;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * S + 8);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&a_full[s], 1);
+      tc::mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&b_full[s], 1);
+      tc::mbar_init(&b_empty[s], 1);
+      tc::mbar_init(&d_full[s], 1);
+      tc::mbar_init(&d_empty[s], 4);
+    }
+    tc::fence_barrier_init();
+    s_abort = 0;
+    tc::prefetch_tmap(&map_t2);
+    tc::prefetch_tmap(&map_g);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abort = &s_abort;
+  const size_t plane = (size_t)C * NP * NP * NP * NP;
+
+  if (warp == 0 && lane == 0) {
+    int it = 0, cur_c = -1, gcount = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+      const int c = u / (NP * 32), i = (u / 32) % NP, mt = u % 32;
+      if (c != cur_c) {
+        const int gs = gcount & 1;
+        if (gcount >= 2 && !tc::mbar_wait(&b_empty[gs], ((gcount >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+        tc::mbar_arrive_expect_tx(&b_full[gs], B_SET);
+        for (int t = 0; t < T; ++t)
+          tc::tma_load_3d(sB + gs * B_SET + t * TILE64, &map_g, &b_full[gs], 0, 0, (TMAX + t) * C + c);
+        cur_c = c;
+        ++gcount;
+      }
+      const int s = it % S;
+      if (it >= S && !tc::mbar_wait(&a_empty[s], ((it / S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::mbar_arrive_expect_tx(&a_full[s], A_STAGE);
+      for (int t = 0; t < T; ++t)
+        for (int h = 0; h < 2; ++h)
+          tc::tma_load_4d(sA + s * A_STAGE + t * TILE128 + h * TILE64, &map_t2, &a_full[s], mt * 128 + h * 64, 0,
+                          c * NP + i, t);
+    }
+  } else if (warp == 1 && lane == 0) {
+    int it = 0, cur_c = -1, gcount = 0, gs = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+      const int c = u / (NP * 32);
+      if (c != cur_c) {
+        if (cur_c >= 0) tc::mma_commit(&b_empty[gs]);
+        gs = gcount & 1;
+        if (!tc::mbar_wait(&b_full[gs], (gcount >> 1) & 1, abort)) { raise_abort(abort, err); break; }
+        cur_c = c;
+        ++gcount;
+      }
+      const int s = it % S, d = it & 1;
+      if (!tc::mbar_wait(&a_full[s], (it / S) & 1, abort)) { raise_abort(abort, err); break; }
+      if (it >= 2 && !tc::mbar_wait(&d_empty[d], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + s * A_STAGE), b0 = tc::smem_u32(sB + gs * B_SET);
+      for (int pr = 0; pr < Products<T>::n; ++pr) {
+        const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 2048, TILE64, 1024);
+          const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
+          tc::mma_bf16(tmem + d * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&a_empty[s]);
+      tc::mma_commit(&d_full[d]);
+    }
+  } else if (warp >= 2) {
+    const int wq = warp & 3, row = wq * 32 + lane;
+    int it = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+      const int c = u / (NP * 32), i = (u / 32) % NP, mt = u % 32;
+      const int d = it & 1;
+      if (!tc::mbar_wait(&d_full[d], (it >> 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::tc_fence_after();
+      float v[64];
+      const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + d * 64;
+      tc::tmem_ld_32x32b_x32(taddr, v);
+      tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+      tc::tmem_ld_wait();
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&d_empty[d]);
+      const size_t off = (((size_t)c * NP + i) * (NP * NP) + (size_t)mt * 128 + row) * NP;
+      store_row_split<T>(t3 + off, plane, v);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stage 4: Sigma[c][i][j] -= sum_K T3[c][i][K] Ws[j][K],  split over K slices
+//
+// Each slice of NP*NP values of K is accumulated in groups of KSUB 64-wide
+// steps: the tensor cores sum one group in FP32 (TMEM, alternating between two
+// accumulators), and the epilogue adds every group into a compensated FP32
+// pair (TwoSum), so that the long sum never runs through a single FP32
+// accumulator.  The slice total enters the FP64 output through atomics.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+template <int T, int KSUB>
+__global__ void __launch_bounds__(192, 1)
+    contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
+                    double *__restrict__ out, int N, int count, int C, int n_units, int *err) {
+  constexpr int S = (T == 2) ? 4 : 3;
+  constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
+  constexpr int NGROUP = KSTEPS / KSUB;
+  constexpr uint32_t STAGE = T * (TILE128 + TILE64);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+  uint64_t *a_full = bar, *a_empty = bar + S, *d_full = bar + 2 * S, *d_empty = bar + 2 * S + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * S + 4);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&a_full[s], 1);
+      tc::mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&d_full[s], 1);
+      tc::mbar_init(&d_empty[s], 4);
+    }
+    tc::fence_barrier_init();
+    s_abort = 0;
+    tc::prefetch_tmap(&map_t3);
+    tc::prefetch_tmap(&map_w);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abort = &s_abort;
+
+  if (warp == 0 && lane == 0) {
+    int g = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int cp = u / NP, l = u % NP;
+      for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
+        const int s = g % S;
+        if (g >= S && !tc::mbar_wait(&a_empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::mbar_arrive_expect_tx(&a_full[s], STAGE);
+        const int k0 = l * NP * NP + ks * NP;
+        uint8_t *st = smem + s * STAGE;
+        for (int t = 0; t < T; ++t) {
+          tc::tma_load_3d(st + t * TILE128, &map_t3, &a_full[s], k0, cp * 128, t);
+          tc::tma_load_3d(st + T * TILE128 + t * TILE64, &map_w, &a_full[s], k0, 0, t);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    int g = 0, grp = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      for (int gi = 0; gi < NGROUP && ok; ++gi, ++grp) {
+        const int d = grp & 1;
+        if (grp >= 2 && !tc::mbar_wait(&d_empty[d], ((grp >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        for (int kq = 0; kq < KSUB; ++kq, ++g) {
+          const int s = g % S;
+          if (!tc::mbar_wait(&a_full[s], (g / S) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t base = tc::smem_u32(smem + s * STAGE);
+          for (int pr = 0; pr < Products<T>::n; ++pr) {
+            const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::smem_desc(base + ta * TILE128 + kk * 32, 16, 1024);
+              const uint64_t bd = tc::smem_desc(base + T * TILE128 + tb * TILE64 + kk * 32, 16, 1024);
+              tc::mma_bf16(tmem + d * 64, ad, bd, kIdescKK, (kq | pr | kk) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(&a_empty[s]);
+        }
+        if (ok) tc::mma_commit(&d_full[d]);
+      }
+    }
+  } else if (warp >= 2) {
+    const int wq = warp & 3, row = wq * 32 + lane;
+    int grp = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int cp = u / NP;
+      float hi[64], lo[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.f;
+      for (int gi = 0; gi < NGROUP; ++gi, ++grp) {
+        const int d = grp & 1;
+        if (!tc::mbar_wait(&d_full[d], (grp >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        float v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + d * 64;
+        tc::tmem_ld_32x32b_x32(taddr, v);
+        tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+        tc::tmem_ld_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&d_empty[d]);
+#pragma unroll
+        for (int j = 0; j < 64; ++j) two_sum_acc(hi[j], lo[j], v[j]);
+      }
+      if (!ok) break;
+      const int c = 2 * cp + row / NP, i = row % NP;
+      if (c < count && i < N) {
+        double *o = out + ((size_t)c * N + i) * N;
+#pragma unroll
+        for (int j = 0; j < 64; ++j)
+          if (j < N) atomicAdd(o + j, -((double)hi[j] + (double)lo[j]));
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stages 1+2 fused: T2[c][i][q][l][n] = sum_{m,k} G[m][n] v[i][m][q][k] G[k][l]
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(320, 1)
+    sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
+                    __nv_bfloat16 *__restrict__ t2, int C, int n_units, int *err) {
+  constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
+  constexpr int A2S = (T == 2) ? 2 : 1;  // buffered MMA2 operands
+  constexpr uint32_t A1_STAGE = T * TILE128, G_SET = 2 * T * TILE64, A2_BUF = T * TILE128;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *sA1 = smem;
+  uint8_t *sG = sA1 + 2 * A1_STAGE;
+  uint8_t *sA2 = sG + GS * G_SET;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sA2 + A2S * A2_BUF);
+  uint64_t *a1_full = bar, *a1_empty = bar + 2, *g_full = bar + 4, *g_empty = bar + 6;
+  uint64_t *d1_full = bar + 8, *d1_empty = bar + 10, *a2_full = bar + 12, *a2_empty = bar + 14;
+  uint64_t *d2_full = bar + 16, *d2_empty = bar + 18;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 20);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(&a1_full[s], 1);
+      tc::mbar_init(&a1_empty[s], 1);
+      tc::mbar_init(&g_full[s], 1);
+      tc::mbar_init(&g_empty[s], 1);
+      tc::mbar_init(&d1_full[s], 1);
+      tc::mbar_init(&d1_empty[s], 4);
+      tc::mbar_init(&a2_full[s], 4);
+      tc::mbar_init(&a2_empty[s], 1);
+      tc::mbar_init(&d2_full[s], 1);
+      tc::mbar_init(&d2_empty[s], 4);
+    }
+    tc::fence_barrier_init();
+    s_abort = 0;
+    tc::prefetch_tmap(&map_v);
+    tc::prefetch_tmap(&map_g);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 256);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;  // D1 buffers at columns 0, 64; D2 at 128, 192
+  volatile int *abort = &s_abort;
+  const size_t plane = (size_t)C * NP * NP * NP * NP;
+
+  if (warp == 0 && lane == 0) {
+    int it = 0, cur_cp = -1, gcount = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+      const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
+      if (cp != cur_cp) {
+        const int gs = gcount % GS;
+        if (gcount >= GS && !tc::mbar_wait(&g_empty[gs], ((gcount / GS) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+        tc::mbar_arrive_expect_tx(&g_full[gs], G_SET);
+        for (int s = 0; s < 2; ++s)
+          for (int t = 0; t < T; ++t)
+            tc::tma_load_3d(sG + gs * G_SET + (s * T + t) * TILE64, &map_g, &g_full[gs], 0, 0,
+                            t * C + 2 * cp + s);
+        cur_cp = cp;
+        ++gcount;
+      }
+      const int st = it & 1;
+      if (it >= 2 && !tc::mbar_wait(&a1_empty[st], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::mbar_arrive_expect_tx(&a1_full[st], A1_STAGE);
+      for (int t = 0; t < T; ++t)
+        tc::tma_load_5d(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 2 * qp, 0, i, t);
+    }
+  } else if (warp == 1 && lane == 0) {
+    int it = 0, cur_cp = -1, gcount = 0, gs = 0;
+    int pend = -1, pend_gs = 0, pend_s = 0;  // job whose MMA2 is not yet issued
+    bool ok = true;
+    auto issue_mma2 = [&](int jj, int jgs, int js) -> bool {
+      const int ab = jj % A2S, db = jj & 1;
+      if (!tc::mbar_wait(&a2_full[ab], (jj / A2S) & 1, abort)) return false;
+      if (jj >= 2 && !tc::mbar_wait(&d2_empty[db], ((jj >> 1) - 1) & 1, abort)) return false;
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA2 + ab * A2_BUF);
+      const uint32_t b0 = tc::smem_u32(sG + jgs * G_SET + js * T * TILE64);
+      for (int pr = 0; pr < Products<T>::n; ++pr) {
+        const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 2048, TILE64, 1024);
+          const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
+          tc::mma_bf16(tmem + 128 + db * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&a2_empty[ab]);
+      tc::mma_commit(&d2_full[db]);
+      return true;
+    };
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+      const int cp = u / (NP * 32);
+      if (cp != cur_cp) {
+        if (pend >= 0) {  // finish the previous pair before its G set can be recycled
+          if (!issue_mma2(pend, pend_gs, pend_s)) { raise_abort(abort, err); ok = false; break; }
+          pend = -1;
+          tc::mma_commit(&g_empty[gs]);
+        }
+        gs = gcount % GS;
+        if (!tc::mbar_wait(&g_full[gs], (gcount / GS) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        cur_cp = cp;
+        ++gcount;
+      }
+      const int st = it & 1;
+      if (!tc::mbar_wait(&a1_full[st], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+      for (int s = 0; s < 2; ++s) {
+        const int j = 2 * it + s, b = j & 1;
+        if (j >= 2 && !tc::mbar_wait(&d1_empty[b], ((j >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(sA1 + st * A1_STAGE);
+        const uint32_t b0 = tc::smem_u32(sG + gs * G_SET + s * T * TILE64);
+        for (int pr = 0; pr < Products<T>::n; ++pr) {
+          const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 32, 16, 1024);
+            const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
+            tc::mma_bf16(tmem + b * 64, ad, bd, kIdescKK, (pr | kk) ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&d1_full[b]);
+        if (s == 1) tc::mma_commit(&a1_empty[st]);
+        if (pend >= 0) {
+          if (!issue_mma2(pend, pend_gs, pend_s)) { raise_abort(abort, err); ok = false; break; }
+        }
+        pend = j;
+        pend_gs = gs;
+        pend_s = s;
+      }
+    }
+    if (ok && pend >= 0 && !issue_mma2(pend, pend_gs, pend_s)) raise_abort(abort, err);
+  } else if (warp >= 2 && warp < 6) {
+    // epilogue 1: D1[(m,q), l] -> A2[(q,l), m] (MN-major, 128-byte swizzle)
+    const int wq = warp & 3, row = wq * 32 + lane;
+    const int m = row >> 1, ql = row & 1;
+    int j = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      for (int s = 0; s < 2; ++s, ++j) {
+        const int b = j & 1;
+        if (!tc::mbar_wait(&d1_full[b], (j >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        float v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + b * 64;
+        tc::tmem_ld_32x32b_x32(taddr, v);
+        tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+        tc::tmem_ld_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&d1_empty[b]);
+        const int ab = j % A2S;
+        if (j >= A2S && !tc::mbar_wait(&a2_empty[ab], ((j / A2S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        uint8_t *dst = sA2 + ab * A2_BUF + ql * TILE64 + m * 128;
+#pragma unroll
+        for (int cch = 0; cch < 8; ++cch) {
+          __nv_bfloat16 p[8][T];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tc::split_f32<T>(v[8 * cch + e], p[e]);
+          const int phys = cch ^ (m & 7);
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            uint4 w;
+            w.x = tc::pack2(p[0][t], p[1][t]);
+            w.y = tc::pack2(p[2][t], p[3][t]);
+            w.z = tc::pack2(p[4][t], p[5][t]);
+            w.w = tc::pack2(p[6][t], p[7][t]);
+            *reinterpret_cast<uint4 *>(dst + t * TILE128 + phys * 16) = w;
+          }
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&a2_full[ab]);
+      }
+    }
+  } else if (warp >= 6) {
+    // epilogue 2: D2[(q,l), n] -> T2[c][i][q][l][n]
+    const int wq = warp & 3, row = wq * 32 + lane;
+    const int ql = row >> 6, l = row & 63;
+    int j = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
+      for (int s = 0; s < 2; ++s, ++j) {
+        const int b = j & 1;
+        if (!tc::mbar_wait(&d2_full[b], (j >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        float v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + 128 + b * 64;
+        tc::tmem_ld_32x32b_x32(taddr, v);
+        tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+        tc::tmem_ld_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&d2_empty[b]);
+        const int c = 2 * cp + s, q = 2 * qp + ql;
+        const size_t off = ((((size_t)c * NP + i) * NP + q) * NP + l) * NP;
+        store_row_split<T>(t2 + off, plane, v);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 256);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// single-tile check of the operand layouts (test hook)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 1)
+    umma_tile_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                     int a_mn_major, float *__restrict__ D, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *sA = smem, *sB = smem + TILE128;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + TILE64);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_barrier_init();
+    s_abort = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 64);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0) {
+    tc::mbar_arrive_expect_tx(&bar[0], TILE128 + TILE64);
+    if (a_mn_major) {
+      tc::tma_load_3d(sA, &map_a, &bar[0], 0, 0, 0);
+      tc::tma_load_3d(sA + TILE64, &map_a, &bar[0], 64, 0, 0);
+    } else {
+      tc::tma_load_3d(sA, &map_a, &bar[0], 0, 0, 0);
+    }
+    tc::tma_load_3d(sB, &map_b, &bar[0], 0, 0, 0);
+    if (tc::mbar_wait(&bar[0], 0, abort)) {
+      tc::tc_fence_after();
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = a_mn_major ? tc::smem_desc(tc::smem_u32(sA) + kk * 2048, TILE64, 1024)
+                                       : tc::smem_desc(tc::smem_u32(sA) + kk * 32, 16, 1024);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + kk * 32, 16, 1024);
+        tc::mma_bf16(tmem, ad, bd, a_mn_major ? kIdescMK : kIdescKK, kk ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[1]);
+    } else {
+      raise_abort(abort, err);
+    }
+  }
+  __syncwarp();
+  const bool done = tc::mbar_wait(&bar[1], 0, abort);
+  if (done) {
+    tc::tc_fence_after();
+    float v[64];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    tc::tmem_ld_32x32b_x32(taddr, v);
+    tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+    tc::tmem_ld_wait();
+    const int row = warp * 32 + lane;
+    for (int j = 0; j < 64; ++j) D[row * 64 + j] = v[j];
+  } else if (lane == 0) {
+    raise_abort(abort, err);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 64);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+              const uint32_t *box) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void *>(base),
+                  reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides_bytes),
+                  reinterpret_cast<const cuuint32_t *>(box), es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+struct TcState {
+  int C = 0;
+  __nv_bfloat16 *Gs = nullptr, *T2 = nullptr, *T3 = nullptr;
+  CUtensorMap map_v, map_g, map_t2, map_t3, map_w;
+};
+
+constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
+
+template <int T>
+size_t smem_sandwich() {
+  const int GS = (T == 2) ? 2 : 1, A2S = (T == 2) ? 2 : 1;
+  return 1024 + 2 * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
+}
+template <int T>
+size_t smem_xform() { return 1024 + ((T == 2) ? 4 : 3) * T * TILE128 + 2 * T * TILE64 + 256; }
+template <int T>
+size_t smem_contract() { return 1024 + ((T == 2) ? 4 : 3) * T * (TILE128 + TILE64) + 256; }
+
+template <int T>
+gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int count, double *d_out) {
+  const int N = ctx->N, C = s->C, sms = ctx->num_sms;
+  const size_t ssw = smem_sandwich<T>(), sxf = smem_xform<T>(), sct = smem_contract<T>();
+  GF2_CK(ctx, cudaFuncSetAttribute(sandwich_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssw));
+  GF2_CK(ctx, cudaFuncSetAttribute(xform_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sxf));
+  GF2_CK(ctx, cudaFuncSetAttribute(contract_kernel<T, kContractGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sct));
+  for (int c0 = 0; c0 < count; c0 += C) {
+    const int cnt = std::min(C, count - c0);
+    const int ce = (cnt + 1) & ~1;
+    GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<<<dim3(C, 2), 256, 0, ctx->stream>>>(N, ctx->M, k0 + c0, cnt, C, d_G, s->Gs)));
+    GF2_CK_LAUNCH(ctx, "split_g_kernel");
+    double *out = d_out + (size_t)c0 * N * N;
+    GF2_CK(ctx, cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cnt * N * N, ctx->stream));
+    const int u1 = (ce / 2) * NP * 32;
+    GF2_PROF(ctx, GF2_K_SANDWICH,
+             (sandwich_kernel<T><<<std::min(u1, sms), 320, ssw, ctx->stream>>>(s->map_v, s->map_g, s->T2, C, u1, ctx->d_err)));
+    GF2_CK_LAUNCH(ctx, "sandwich_kernel");
+    const int u2 = ce * NP * 32;
+    GF2_PROF(ctx, GF2_K_XFORM,
+             (xform_kernel<T><<<std::min(u2, sms), 192, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->T3, C, u2, ctx->d_err)));
+    GF2_CK_LAUNCH(ctx, "xform_kernel");
+    const int u3 = (ce / 2) * NP;
+    GF2_PROF(ctx, GF2_K_CONTRACT,
+             (contract_kernel<T, kContractGroup><<<std::min(u3, sms), 192, sct, ctx->stream>>>(
+                 s->map_t3, s->map_w, out, N, cnt, C, u3, ctx->d_err)));
+    GF2_CK_LAUNCH(ctx, "contract_kernel");
+  }
+  return GF2_OK;
+}
+
+TcState *tc_state(gf2_ctx *ctx) { return reinterpret_cast<TcState *>(ctx->d_tc_ws); }
+
+}  // namespace
+
+gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
+  if (ctx->N > NP) return GF2_ERR_UNSUPPORTED;
+  if (!encode_fn()) return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+  const size_t bytes = TMAX * kPlane4 * sizeof(__nv_bfloat16);
+  if (!ctx->d_v_split) GF2_CK(ctx, cudaMalloc(&ctx->d_v_split, bytes));
+  if (!ctx->d_wt_split) GF2_CK(ctx, cudaMalloc(&ctx->d_wt_split, bytes));
+  const int blocks = 8 * ctx->num_sms;
+  // integrals in the orthonormal (Loewdin) basis when the overlap is known
+  double *vsrc = ctx->d_v, *vorth = nullptr;
+  if (ctx->d_Shalf) {
+    const size_t n4 = (size_t)ctx->N * ctx->N * ctx->N * ctx->N;
+    GF2_CK(ctx, cudaMalloc(&vorth, n4 * sizeof(double)));
+    gf2_status st = gf2_orth_transform_v(ctx, vorth);
+    if (st != GF2_OK) {
+      cudaFree(vorth);
+      return st;
+    }
+    vsrc = vorth;
+  }
+  split_v_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, (__nv_bfloat16 *)ctx->d_v_split);
+  GF2_CK_LAUNCH(ctx, "split_v_kernel");
+  split_w_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, (__nv_bfloat16 *)ctx->d_wt_split);
+  GF2_CK_LAUNCH(ctx, "split_w_kernel");
+  if (vorth) {
+    GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(vorth);
+  }
+  ctx->split_terms = TMAX;
+  return GF2_OK;
+}
+
+static gf2_status tc_workspace(gf2_ctx *ctx) {
+  if (ctx->d_tc_ws) return GF2_OK;
+  TcState *s = new (std::nothrow) TcState();
+  if (!s) return gf2_fail(ctx, GF2_ERR_NOMEM, "tc state");
+  s->C = std::max(2, std::min(32, ((ctx->n_tau + 1) / 2) * 2));
+  const int C = s->C;
+  const size_t gbytes = (size_t)2 * TMAX * C * NP * NP * sizeof(__nv_bfloat16);
+  const size_t ibytes = (size_t)TMAX * C * kPlane4 * sizeof(__nv_bfloat16);
+  cudaError_t e = cudaMalloc(&s->Gs, gbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->T2, ibytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->T3, ibytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->T2, 0, ibytes, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->T3, 0, ibytes, ctx->stream);
+  if (e != cudaSuccess) {
+    if (s->Gs) cudaFree(s->Gs);
+    if (s->T2) cudaFree(s->T2);
+    if (s->T3) cudaFree(s->T3);
+    delete s;
+    return gf2_cuda_fail(ctx, e, "tc workspace");
+  }
+  bool ok = true;
+  {  // v: dims (k, q, m, i, t), box (64, 2, 64, 1, 1) -> rows (m, q) of 64 k
+    uint64_t dims[5] = {NP, NP, NP, NP, TMAX};
+    uint64_t str[4] = {NP * 2, NP * NP * 2, (uint64_t)NP * NP * NP * 2, kPlane4 * 2};
+    uint32_t box[5] = {64, 2, 64, 1, 1};
+    ok &= make_map(&s->map_v, ctx->d_v_split, 5, dims, str, box);
+  }
+  {  // G sets: dims (64, 64, 2*TMAX*C), box (64, 64, 1)
+    uint64_t dims[3] = {NP, NP, (uint64_t)2 * TMAX * C};
+    uint64_t str[2] = {NP * 2, NP * NP * 2};
+    uint32_t box[3] = {64, 64, 1};
+    ok &= make_map(&s->map_g, s->Gs, 3, dims, str, box);
+  }
+  {  // T2: dims ((l,n) 4096, q 64, (c,i) C*64, t), box (64, 64, 1, 1): MN-major tiles
+    uint64_t dims[4] = {NP * NP, NP, (uint64_t)C * NP, TMAX};
+    uint64_t str[3] = {NP * NP * 2, (uint64_t)NP * NP * NP * 2, (uint64_t)C * kPlane4 * 2};
+    uint32_t box[4] = {64, 64, 1, 1};
+    ok &= make_map(&s->map_t2, s->T2, 4, dims, str, box);
+  }
+  {  // T3: dims (K = NP^3, rows (c,i) C*64, t), box (64, 128, 1)
+    uint64_t dims[3] = {(uint64_t)NP * NP * NP, (uint64_t)C * NP, TMAX};
+    uint64_t str[2] = {(uint64_t)NP * NP * NP * 2, (uint64_t)C * kPlane4 * 2};
+    uint32_t box[3] = {64, 128, 1};
+    ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box);
+  }
+  {  // W: dims (K = NP^3, j 64, t), box (64, 64, 1)
+    uint64_t dims[3] = {(uint64_t)NP * NP * NP, NP, TMAX};
+    uint64_t str[2] = {(uint64_t)NP * NP * NP * 2, kPlane4 * 2};
+    uint32_t box[3] = {64, 64, 1};
+    ok &= make_map(&s->map_w, ctx->d_wt_split, 3, dims, str, box);
+  }
+  if (!ok) {
+    cudaFree(s->Gs);
+    cudaFree(s->T2);
+    cudaFree(s->T3);
+    delete s;
+    return gf2_fail(ctx, GF2_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  }
+  ctx->d_tc_ws = s;
+  ctx->tc_chunk = C;
+  return GF2_OK;
+}
+
+void gf2_tc_release(gf2_ctx *ctx) {
+  TcState *s = tc_state(ctx);
+  if (!s) return;
+  cudaFree(s->Gs);
+  cudaFree(s->T2);
+  cudaFree(s->T3);
+  delete s;
+  ctx->d_tc_ws = nullptr;
+}
+
+gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, double *d_out, int prec) {
+  if (ctx->N > NP || !ctx->d_v_split)
+    return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "tensor-core path needs N <= 64 and gf2_set_integrals");
+  gf2_status st = tc_workspace(ctx);
+  if (st != GF2_OK) return st;
+  GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  TcState *s = tc_state(ctx);
+  // in the orthonormal basis: G' = S^{1/2} G S^{1/2} in, Sigma = S^{1/2} Sigma' S^{1/2} out
+  const double *G_use = d_G;
+  double *out_use = d_out;
+  if (ctx->d_Shalf) {
+    double *Go = nullptr;
+    if ((st = gf2_orth_transform_g(ctx, d_G, k0, count, &Go)) != GF2_OK) return st;
+    G_use = Go;
+    out_use = ctx->d_orth_ws + 2 * (size_t)ctx->n_tau * ctx->N * ctx->N;
+  }
+  st = (prec == GF2_PREC_BF16X3) ? run_chunks<2>(ctx, s, G_use, k0, count, out_use)
+                                 : run_chunks<3>(ctx, s, G_use, k0, count, out_use);
+  if (st != GF2_OK) return st;
+  if (ctx->d_Shalf && (st = gf2_orth_sigma_to_ao(ctx, out_use, count, d_out)) != GF2_OK) return st;
+  int flag = 0;
+  GF2_CK(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (flag) return gf2_fail(ctx, GF2_ERR_TIMEOUT, "tensor-core Sigma: a pipeline wait timed out");
+  return GF2_OK;
+}
+
+// test hook: one 128x64x64 BF16 tile through TMA, tcgen05.mma and tcgen05.ld
+extern "C" gf2_status gf2_test_umma_tile(int a_mn_major, const void *d_A, const void *d_B, float *d_D,
+                                         int *d_err, void *stream) {
+  if (!d_A || !d_B || !d_D || !d_err) return GF2_ERR_ARG;
+  if (!encode_fn()) return GF2_ERR_UNSUPPORTED;
+  CUtensorMap ma, mb;
+  bool ok;
+  if (a_mn_major) {  // A stored [K=64][M=128]: dims (128, 64, 1), box (64, 64, 1)
+    uint64_t dims[3] = {128, 64, 1};
+    uint64_t str[2] = {128 * 2, 128 * 64 * 2};
+    uint32_t box[3] = {64, 64, 1};
+    ok = make_map(&ma, d_A, 3, dims, str, box);
+  } else {  // A stored [M=128][K=64]: dims (64, 128, 1), box (64, 128, 1)
+    uint64_t dims[3] = {64, 128, 1};
+    uint64_t str[2] = {64 * 2, 64 * 128 * 2};
+    uint32_t box[3] = {64, 128, 1};
+    ok = make_map(&ma, d_A, 3, dims, str, box);
+  }
+  uint64_t dims[3] = {64, 64, 1};
+  uint64_t str[2] = {64 * 2, 64 * 64 * 2};
+  uint32_t box[3] = {64, 64, 1};
+  ok = ok && make_map(&mb, d_B, 3, dims, str, box);
+  if (!ok) return GF2_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = 1024 + TILE128 + TILE64 + 256;
+  if (cudaFuncSetAttribute(umma_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GF2_ERR_CUDA;
+  umma_tile_kernel<<<1, 128, smem, st>>>(ma, mb, a_mn_major, d_D, d_err);
+  if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GF2_ERR_CUDA;
+  return GF2_OK;
 }

@@ -318,9 +318,10 @@ extern "C" gf2_status gf2_fft_iw_to_tau(gf2_ctx *ctx, const double *d_X_iw, cons
   const int E = pick_elems_per_cta(N2, M);
   const size_t smem = (size_t)E * M * sizeof(double2) + sizeof(double) * 4 * E;
   GF2_CK(ctx, cudaFuncSetAttribute(iw_to_tau_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  iw_to_tau_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
-      N2, M, ctx->log2M, ctx->n_iw, E, ctx->beta, reinterpret_cast<const double2 *>(d_X_iw), coef,
-      ctx->d_iw_pole, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, d_X_tau);
+  GF2_PROF(ctx, GF2_K_IW2TAU,
+           (iw_to_tau_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
+               N2, M, ctx->log2M, ctx->n_iw, E, ctx->beta, reinterpret_cast<const double2 *>(d_X_iw), coef,
+               ctx->d_iw_pole, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, d_X_tau)));
   GF2_CK_LAUNCH(ctx, "iw_to_tau_kernel");
   return GF2_OK;
 }
@@ -332,9 +333,10 @@ extern "C" gf2_status gf2_fft_tau_to_iw(gf2_ctx *ctx, const double *d_X_tau, dou
   const int E = pick_elems_per_cta(N2, M);
   const size_t smem = (size_t)E * M * sizeof(double2) + sizeof(double) * 8 * E;
   GF2_CK(ctx, cudaFuncSetAttribute(tau_to_iw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tau_to_iw_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
-      N2, M, ctx->log2M, ctx->n_iw, E, d_X_tau, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->d_t2w_w,
-      ctx->d_t2w_corr, reinterpret_cast<double2 *>(d_X_iw));
+  GF2_PROF(ctx, GF2_K_TAU2IW,
+           (tau_to_iw_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
+               N2, M, ctx->log2M, ctx->n_iw, E, d_X_tau, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->d_t2w_w,
+               ctx->d_t2w_corr, reinterpret_cast<double2 *>(d_X_iw))));
   GF2_CK_LAUNCH(ctx, "tau_to_iw_kernel");
   if (d_sig12) {
     sigma_ends_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(N2, M, ctx->beta / M, d_X_tau, d_sig12);

@@ -10,8 +10,10 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import (GF2_PREC_BF16X3, GF2_PREC_FP64, Context, gf2_energy, gf2_fft_iw_to_tau,
-               gf2_fft_tau_to_iw, gf2_fock, gf2_mu_search, gf2_set_integrals, gf2_sigma_tau,
+import numpy as np
+
+from . import (GF2_PREC_BF16X3, GF2_PREC_FP64, Context, gf2_combine, gf2_energy, gf2_fft_iw_to_tau,
+               gf2_fft_tau_to_iw, gf2_fock, gf2_gram, gf2_mu_search, gf2_set_integrals, gf2_set_overlap, gf2_sigma_tau,
                gf2_tail_moments)
 
 
@@ -62,6 +64,7 @@ def start(sys, prec=GF2_PREC_FP64):
     n, nt, nw = sys.nbf, sys.n_tau, sys.n_iw
     ctx = Context(n, nt, nw, sys.beta)
     gf2_set_integrals(ctx.handle, sys.v)
+    gf2_set_overlap(ctx.handle, sys.S)
     dev = sys.S.device
     run = GF2Run(ctx=ctx, sys=sys, prec=prec)
     run.F = sys.F0.clone()
@@ -76,23 +79,52 @@ def start(sys, prec=GF2_PREC_FP64):
     return run
 
 
-def inner_loop(run, tol=1e-10, max_iter=200, mu_tol=1e-10):
-    """Steps 2.a-2.b: mu search and Fock rebuild until F stops changing."""
+def _diis_coefficients(gram):
+    """Pulay weights: minimise |sum c_a R_a| subject to sum c_a = 1 (host, tiny)."""
+    m = len(gram)
+    B = np.zeros((m + 1, m + 1))
+    B[:m, :m] = np.asarray(gram)
+    B[m, :m] = B[:m, m] = -1.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = -1.0
+    return np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
+
+
+def inner_loop(run, tol=1e-8, max_iter=200, mu_tol=1e-10, diis=8):
+    """Steps 2.a-2.b: mu search and Fock rebuild until the Fock residual
+    R = F(P(F)) - F has Frobenius norm below ``tol``; the next F is the Pulay
+    extrapolation of the last ``diis`` rebuilt matrices.  G, P and mu are
+    re-evaluated at the converged F."""
     s = run.sys
-    F_new = torch.empty_like(run.F)
+    h = run.ctx.handle
+    hist_F, hist_R = [], []
     for _ in range(max_iter):
-        run.mu, nev = gf2_mu_search(run.ctx.handle, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
+        run.mu, nev = gf2_mu_search(h, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
                                     run.G_iw, run.P, tol=mu_tol)
         run.mu_evals.append(nev)
-        gf2_fock(run.ctx.handle, s.h, run.P, F_new)
-        diff = (F_new - run.F).abs().max().item()
-        run.F.copy_(F_new)
-        if diff < tol:
-            # G and P at the final F
-            run.mu, nev = gf2_mu_search(run.ctx.handle, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec,
-                                        run.mu, run.G_iw, run.P, tol=mu_tol)
+        F_out = torch.empty_like(run.F)
+        gf2_fock(h, s.h, run.P, F_out)
+        R = torch.empty_like(run.F)
+        gf2_combine(h, [1.0, -1.0], [F_out, run.F], R)
+        if gf2_gram(h, [R])[0][0] ** 0.5 < tol:
+            run.F = F_out
+            run.mu, nev = gf2_mu_search(h, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
+                                        run.G_iw, run.P, tol=mu_tol)
             run.mu_evals.append(nev)
             return
+        if diis > 0:
+            hist_F.append(F_out)
+            hist_R.append(R)
+            hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
+            if len(hist_F) > 1:
+                c = _diis_coefficients(gf2_gram(h, hist_R))
+                F_next = torch.empty_like(run.F)
+                gf2_combine(h, list(c), hist_F, F_next)
+                run.F = F_next
+            else:
+                run.F = F_out
+        else:
+            run.F = F_out
     raise RuntimeError("inner loop did not converge")
 
 
@@ -110,7 +142,7 @@ def self_energy_step(run, damping=1.0):
     if damping < 1.0 and run.sig12 is not None:
         new = torch.empty_like(run.Sigma_tau)
         gf2_sigma_tau(run.ctx.handle, run.G_tau, new, run.prec)
-        run.Sigma_tau.mul_(1.0 - damping).add_(new, alpha=damping)
+        gf2_combine(run.ctx.handle, [damping, 1.0 - damping], [new, run.Sigma_tau], run.Sigma_tau)
     else:
         gf2_sigma_tau(run.ctx.handle, run.G_tau, run.Sigma_tau, run.prec)
     if run.sig12 is None:
@@ -118,7 +150,7 @@ def self_energy_step(run, damping=1.0):
     gf2_fft_tau_to_iw(run.ctx.handle, run.Sigma_tau, run.Sigma_iw, run.sig12)
 
 
-def run_gf2(sys, prec=GF2_PREC_FP64, max_outer=30, e_tol=1e-8, damping=1.0, inner_tol=1e-10, callback=None):
+def run_gf2(sys, prec=GF2_PREC_FP64, max_outer=30, e_tol=1e-8, damping=1.0, inner_tol=1e-8, callback=None):
     run = start(sys, prec)
     inner_loop(run, inner_tol)
     run.energies.append(energy(run))

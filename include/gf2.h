@@ -184,6 +184,29 @@ gf2_status gf2_combine(gf2_ctx *ctx, int n, const double *coef, const double *co
                        long long count, double *d_out);
 gf2_status gf2_gram(gf2_ctx *ctx, int n, const double *const *d_vecs, long long count, double *gram_out);
 
+/* Allocation-free Galitskii-Migdal energy (no counterpart in the paper).
+ * Same inputs, outputs and arithmetic as gf2_energy, but without a context
+ * and without allocating: for callers that cannot call cudaMalloc -- code
+ * running while a CUDA graph is captured, inside host callbacks, or in hosts
+ * that give the library a fixed memory budget and forbid the device
+ * allocator.  Its scratch (per-frequency partial sums, S^-1, the results) is
+ * a fixed __device__ array of 65536 + 112*112 + 8 doubles (about 610 KB) that
+ * every device loading the library keeps until the process exits.
+ *   Limits: n_bf <= 112 and n_iw <= 65536, else GF2_ERR_UNSUPPORTED before any
+ *   launch; NULL pointers or bad sizes give GF2_ERR_ARG; CUDA failures
+ *   GF2_ERR_CUDA.  d_sig12 may be NULL (no tail term).
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  Every call overwrites the shared array and fully rewrites what it
+ *   reads, so consecutive calls are independent; calls that overlap on the GPU
+ *   (other streams or threads at the same time) race on it.
+ *   Runs on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *   synchronizes it to return the two host scalars. */
+gf2_status gf2_energy_noalloc(int n_bf, int n_iw, double beta, const double *d_h, const double *d_F,
+                              const double *d_P, const double *d_S, const double *d_G_iw,
+                              const double *d_Sigma_iw, const double *d_sig12, double *e_one_body,
+                              double *e_two_body, void *stream);
+
 /* Tracing (no counterpart in the paper).  gf2_profile(ctx, 1) clears the
  * counters and starts timing every kernel launch of the context with CUDA
  * events on its stream (0 stops; launches are counted either way).

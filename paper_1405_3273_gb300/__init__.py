@@ -50,6 +50,7 @@ _SIGS = {
     "gf2_energy": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "gf2_combine": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.c_longlong, _P],
     "gf2_gram": [_P, _I, ctypes.POINTER(_P), ctypes.c_longlong, ctypes.POINTER(_D)],
+    "gf2_energy_noalloc": [_I, _I, _D, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
     "gf2_profile": [_P, _I],
     "gf2_profile_report": [_P, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -180,6 +181,16 @@ def gf2_energy(ctx, h, F, P, S, G_iw, Sigma_iw, sig12):
     _check(lib().gf2_energy(ctx, _ptr(h, _F64), _ptr(F, _F64), _ptr(P, _F64), _ptr(S, _F64),
                             _ptr(G_iw, _C128), _ptr(Sigma_iw, _C128), _ptr(sig12, _F64),
                             ctypes.byref(e1), ctypes.byref(e2)), ctx)
+    return e1.value, e2.value
+
+
+def gf2_energy_noalloc(n_bf, n_iw, beta, h, F, P, S, G_iw, Sigma_iw, sig12):
+    """Allocation-free gf2_energy (no context); see include/gf2.h."""
+    e1, e2 = ctypes.c_double(), ctypes.c_double()
+    st = lib().gf2_energy_noalloc(int(n_bf), int(n_iw), float(beta), _ptr(h, _F64), _ptr(F, _F64),
+                                  _ptr(P, _F64), _ptr(S, _F64), _ptr(G_iw, _C128), _ptr(Sigma_iw, _C128),
+                                  _ptr(sig12, _F64), ctypes.byref(e1), ctypes.byref(e2), _stream())
+    _check(st, None)
     return e1.value, e2.value
 
 

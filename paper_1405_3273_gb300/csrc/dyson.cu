@@ -468,3 +468,107 @@ extern "C" gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *
   *e_two_body = ctx->h_pinned[1];
   return GF2_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of gf2_energy.
+//
+// For callers that must not allocate device memory at all -- code that runs
+// while a CUDA graph is being captured or replayed, inside a host callback,
+// or in an embedding that owns a fixed memory budget and forbids calls into
+// the device allocator -- this entry point needs no context and makes no
+// cudaMalloc/cudaFree (nor any allocating library call).  Its scratch (one
+// partial sum per frequency, S^-1 and the two results) lives in a file-scope
+// __device__ array of fixed size, present on every device that loads the
+// library until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int kNoallocMaxN = GF2_MAX_N;                 // 112
+constexpr int kNoallocMaxIw = 65536;
+constexpr size_t kNoallocDoubles = (size_t)kNoallocMaxIw + (size_t)kNoallocMaxN * kNoallocMaxN + 8;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_addr[256] = {};
+
+// device address of g_noalloc_scratch on the current device, looked up once per device
+gf2_status noalloc_scratch(double **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GF2_ERR_CUDA;
+  if (dev < 0 || dev >= 256) return GF2_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GF2_ERR_CUDA;
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return GF2_OK;
+}
+
+// S^-1 by Gauss-Jordan in shared memory (S symmetric positive definite)
+__global__ void noalloc_inverse_kernel(const double *A, double *Ainv, int n) {
+  extern __shared__ double noalloc_sm[];
+  double *a = noalloc_sm, *col = noalloc_sm + n * n, *row = col + n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) a[e] = A[e];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = a[i * n + k];
+    __syncthreads();
+    const double p = 1.0 / col[k];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double r = (j == k) ? p : a[k * n + j] * p;
+      row[j] = r;
+      a[k * n + j] = r;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      if (i == k) continue;
+      if (j == k) a[e] = -col[i] * p;
+      else a[e] -= col[i] * row[j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ainv[e] = a[e];
+}
+
+}  // namespace
+
+extern "C" gf2_status gf2_energy_noalloc(int n_bf, int n_iw, double beta, const double *d_h, const double *d_F,
+                                         const double *d_P, const double *d_S, const double *d_G_iw,
+                                         const double *d_Sigma_iw, const double *d_sig12, double *e_one_body,
+                                         double *e_two_body, void *stream) {
+  if (!d_h || !d_F || !d_P || !d_S || !d_G_iw || !d_Sigma_iw || !e_one_body || !e_two_body) return GF2_ERR_ARG;
+  if (n_bf < 1 || n_iw < 1 || !(beta > 0.0) || !std::isfinite(beta)) return GF2_ERR_ARG;
+  if (n_bf > kNoallocMaxN || n_iw > kNoallocMaxIw) return GF2_ERR_UNSUPPORTED;
+  double *scratch = nullptr;
+  gf2_status st = noalloc_scratch(&scratch);
+  if (st != GF2_OK) return st;
+  double *partial = scratch;                            // [n_iw]
+  double *sinv = scratch + kNoallocMaxIw;               // [N][N]
+  double *res = sinv + (size_t)kNoallocMaxN * kNoallocMaxN;  // [2]
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  energy_partial_kernel<<<n_iw, 256, 0, s>>>(n_bf, reinterpret_cast<const double2 *>(d_G_iw),
+                                             reinterpret_cast<const double2 *>(d_Sigma_iw), partial);
+  if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+  if (d_sig12) {
+    const size_t smem = sizeof(double) * ((size_t)n_bf * n_bf + 2 * (size_t)n_bf);
+    if (cudaFuncSetAttribute(noalloc_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GF2_ERR_CUDA;
+    noalloc_inverse_kernel<<<1, 256, smem, s>>>(d_S, sinv, n_bf);
+    if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+  }
+  energy_final_kernel<<<1, 256, 0, s>>>(n_bf, n_iw, beta, partial, d_P, d_h, d_F, sinv, d_sig12, res);
+  if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+  double host[2];
+  if (cudaMemcpyAsync(host, res, sizeof host, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GF2_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GF2_ERR_CUDA;
+  *e_one_body = host[0];
+  *e_two_body = host[1];
+  return GF2_OK;
+}

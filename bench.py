@@ -50,7 +50,16 @@ def parse():
     ap.add_argument("--fp64-points", type=int, default=8, help="tau points for the FP64 path timing")
     ap.add_argument("--no-energy-check", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=4, help="tau points of the oracle CPU sample")
-    return ap.parse_args()
+    ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
+    ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
+    args = ap.parse_args()
+    if args.n_tau:
+        WORKLOAD["n_tau"] = args.n_tau
+    if args.n_iw:
+        WORKLOAD["n_iw"] = args.n_iw
+    return args
 
 
 # --------------------------------------------------------------------------- setup
@@ -221,6 +230,12 @@ def run_ours(args, rank, world, dist):
         t = torch.tensor([ms_step], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t[0])
+    if args.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms_step, "sigma_ms": sigma_ms,
+                              "kernels": {k: v for k, v in prof.items()}, "launches": launches}))
+        ctx.close()
+        return
 
     # end to end: host buffers in, host scalars and P out, copies inside the timed region
     G_host = G_iw0.cpu().pin_memory()
@@ -271,7 +286,8 @@ def run_ours(args, rank, world, dist):
         e1, e2 = g.gf2_energy(h, hcore, F0, P64, S, G64, Sig_iw, sig12)
         e64 = s.e_nuc + e1 + e2
         energy_check = {"E_split": log[-1][0], "E_fp64_gpu": e64, "abs_dE": abs(log[-1][0] - e64),
-                        "max_abs_dP": (P - P64).abs().max().item()}
+                        "max_abs_dP": (P - P64).abs().max().item(), "mu_split": log[-1][1], "mu_fp64": mu64,
+                        "n_split": float(torch.trace(P @ S)), "n_fp64": float(torch.trace(P64 @ S))}
 
     hbm_gbs, bf16_burst, bf16_sust, peak_kind = measured_peaks()
     useful = flops_tau * n_tau
@@ -313,7 +329,8 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
-        "config": {"workload": "H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, n_tau=4097, n_iw=8192",
+        "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, "
+                                f"n_tau={n_tau}, n_iw={n_iw}"),
                    "step": "one GF2 outer iteration, all hot-path rows",
                    "l2": "inputs larger than L2 (G(iw) 537 MB, intermediates 6 GB)",
                    "parallelism": f"replicas x{world}"},
@@ -409,7 +426,8 @@ def run_reference(args, rank, world, dist):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, n_tau=4097, n_iw=8192",
+            "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, "
+                                f"n_tau={n_tau}, n_iw={n_iw}"),
                        "parallelism": "CPU oracle on the host cores"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "each step: the oracle's rows timed on bounded samples (Sigma on a few tau "

@@ -11,9 +11,8 @@
 //
 // Dyson.  A(i w) = (i w + mu) S - F - Sigma(i w) is complex symmetric with
 // Im A = w S - Im Sigma positive definite for w > 0 (Im Sigma(i w) <= 0 for a
-// causal self-energy), so Gauss-Jordan elimination without pivoting is stable;
-// pivots are still checked and a tiny one is reported as GF2_ERR_NONFINITE.
-// One CTA per frequency, the matrix held in shared memory.
+// causal self-energy), so elimination without pivoting is stable; pivots are
+// still checked and a tiny one is reported as GF2_ERR_NONFINITE.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,49 +48,105 @@ __global__ void moments_kernel(int N2, double mu, const double *basis, double *m
   mom[3 * N2 + e] = A3 - 3.0 * mu * A2 + 3.0 * mu * mu * A1 - mu * mu * mu * A0 + B2 - 2.0 * mu * B1 + B3;
 }
 
-__global__ void dyson_kernel(int N, double beta, double mu, const double *__restrict__ S,
-                             const double *__restrict__ F, const double2 *__restrict__ Sig,
-                             double2 *__restrict__ G, int *flag) {
-  extern __shared__ double2 sm[];
+// Inverse of the complex symmetric A(i w_n) by symmetric sweeps (Gauss-Jordan
+// without pivoting, which keeps A symmetric at every step): sweeping pivot k
+// maps a_kk -> -1/a_kk, a_ik -> a_ik/a_kk and a_ij -> a_ij - a_ik a_kj / a_kk;
+// after all N pivots the matrix holds -A^-1.  Only the upper triangle is
+// updated (N^3/2 complex multiply-adds instead of N^3); it is loaded as the
+// symmetric part (A_ij + A_ji)/2, so inputs whose triangles differ by
+// rounding (a split-precision Sigma) enter through their symmetric part.  Each thread keeps its
+// share of the triangle in registers; the pivot column is published through
+// shared memory once per step.  One CTA per frequency.
+constexpr int kDysonThreads = 512;
+constexpr int kDysonMaxPerThread = (GF2_MAX_N * (GF2_MAX_N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
+
+template <int PER>
+__global__ void __launch_bounds__(kDysonThreads, 1)
+    dyson_kernel(int N, double beta, double mu, const double *__restrict__ S, const double *__restrict__ F,
+                 const double2 *__restrict__ Sig, double2 *__restrict__ G, int *flag) {
+  __shared__ double2 v[GF2_MAX_N];  // pivot column a_ik
+  __shared__ double2 w[GF2_MAX_N];  // a_ik / a_kk
+  __shared__ double2 pinv;
+  __shared__ int bad;
   const int N2 = N * N;
-  double2 *a = sm, *col = sm + N2, *row = col + N;
   const long long n = blockIdx.x;
-  const double w = (2.0 * n + 1.0) * M_PI / beta;
-  for (int e = threadIdx.x; e < N2; e += blockDim.x) {
-    const double s = S[e];
-    double2 v = make_double2(mu * s - F[e], w * s);
-    if (Sig) v = csub(v, Sig[n * N2 + e]);
-    a[e] = v;
+  const double om = (2.0 * n + 1.0) * M_PI / beta;
+  const int ntri = N * (N + 1) / 2;
+  double2 a[PER];
+  int ij[PER];  // (i << 8) | j, or -1
+  if (threadIdx.x == 0) bad = 0;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = threadIdx.x + r * kDysonThreads;
+    ij[r] = -1;
+    a[r] = make_double2(0.0, 0.0);
+    if (e < ntri) {
+      // row-major upper triangle: row i holds N - i elements
+      int i = 0, rem = e;
+      while (rem >= N - i) {
+        rem -= N - i;
+        ++i;
+      }
+      const int j = i + rem;
+      ij[r] = (i << 8) | j;
+      // the symmetric part of A (S, F and Sigma are symmetric up to rounding)
+      const int idx = i * N + j, idt = j * N + i;
+      const double sv = 0.5 * (S[idx] + S[idt]);
+      double2 x = make_double2(mu * sv - 0.5 * (F[idx] + F[idt]), om * sv);
+      if (Sig) x = csub(x, cscale(cadd(Sig[n * N2 + idx], Sig[n * N2 + idt]), 0.5));
+      a[r] = x;
+    }
   }
-  __syncthreads();
-  bool bad = false;
   for (int k = 0; k < N; ++k) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) col[i] = a[i * N + k];
-    __syncthreads();
-    const double2 piv = col[k];
-    const double mag = fabs(piv.x) + fabs(piv.y);
-    if (!(mag > 1e-280)) bad = true;
-    const double2 p = crecip(piv);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const double2 r = (j == k) ? p : cmul(a[k * N + j], p);
-      row[j] = r;
-      a[k * N + j] = r;
+    // 1. publish the pivot column v_i = a_ik (= a_ki) and 1/a_kk
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      if (ij[r] < 0) continue;
+      const int i = ij[r] >> 8, j = ij[r] & 255;
+      if (j == k) {
+        v[i] = a[r];
+        if (i == k) {
+          if (!(fabs(a[r].x) + fabs(a[r].y) > 1e-280)) bad = 1;
+          pinv = crecip(a[r]);
+        }
+      } else if (i == k) {
+        v[j] = a[r];
+      }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < N2; e += blockDim.x) {
-      const int i = e / N, j = e - i * N;
-      if (i == k) continue;
-      if (j == k) {
-        const double2 t = cmul(col[i], p);
-        a[e] = make_double2(-t.x, -t.y);
+    // 2. scaled pivot column w_i = a_ik / a_kk
+    const double2 p = pinv;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = cmul(v[i], p);
+    __syncthreads();
+    // 3. rank-1 update of the upper triangle, a_ij -= w_i a_kj (four FP64 FMAs)
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      if (ij[r] < 0) continue;
+      const int i = ij[r] >> 8, j = ij[r] & 255;
+      if (i == k || j == k) {
+        if (i == j) a[r] = make_double2(-p.x, -p.y);
+        else a[r] = w[i == k ? j : i];
       } else {
-        a[e] = csub(a[e], cmul(col[i], row[j]));
+        const double2 wi = w[i], vj = v[j];
+        double2 x = a[r];
+        x.x = fma(-wi.x, vj.x, x.x);
+        x.x = fma(wi.y, vj.y, x.x);
+        x.y = fma(-wi.x, vj.y, x.y);
+        x.y = fma(-wi.y, vj.x, x.y);
+        a[r] = x;
       }
     }
     __syncthreads();
   }
   if (bad && threadIdx.x == 0) atomicExch(flag, 1);
-  for (int e = threadIdx.x; e < N2; e += blockDim.x) G[n * N2 + e] = a[e];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    if (ij[r] < 0) continue;
+    const int i = ij[r] >> 8, j = ij[r] & 255;
+    const double2 g = make_double2(-a[r].x, -a[r].y);
+    G[n * N2 + (size_t)i * N + j] = g;
+    if (i != j) G[n * N2 + (size_t)j * N + i] = g;
+  }
 }
 
 // partial[chunk][e] = sum_{n in chunk} Re G_e(n)
@@ -287,13 +342,19 @@ gf2_status launch_moments(gf2_ctx *ctx, double mu, double *mom) {
 gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *F, const double *Sig,
                         double *G) {
   const int N = ctx->N;
-  const size_t smem = sizeof(double2) * ((size_t)N * N + 2 * N);
-  GF2_CK(ctx, cudaFuncSetAttribute(dyson_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int per = (N * (N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
   GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-  GF2_PROF(ctx, GF2_K_DYSON,
-           (dyson_kernel<<<ctx->n_iw, 256, smem, ctx->stream>>>(N, ctx->beta, mu, S, F,
-                                                                reinterpret_cast<const double2 *>(Sig),
-                                                                reinterpret_cast<double2 *>(G), ctx->d_err)));
+  const double2 *sg = reinterpret_cast<const double2 *>(Sig);
+  double2 *gg = reinterpret_cast<double2 *>(G);
+  const int nb = ctx->n_iw;
+  cudaStream_t st = ctx->stream;
+  if (per <= 1) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 2) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 4) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<4><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 5) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<5><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 9) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<9><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 16) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<16><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<kDysonMaxPerThread><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
   GF2_CK_LAUNCH(ctx, "dyson_kernel");
   return GF2_OK;
 }

@@ -187,3 +187,29 @@ gf2_status gf2_orth_sigma_to_ao(gf2_ctx *ctx, const double *d_Sig_orth, int coun
   double *tmp = ctx->d_orth_ws + grid;
   return sandwich_batch(ctx, ctx->d_Shalf, d_Sig_orth, ctx->d_Shalf, tmp, d_out, count);
 }
+
+namespace {
+// X <- (X + X^T)/2 for `count` N x N matrices
+__global__ void symmetrize_kernel(int N, long long count, double *X) {
+  const long long N2 = (long long)N * N;
+  const long long total = count * N2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / N2;
+    const int r = (int)(e % N2), i = r / N, j = r % N;
+    if (i >= j) continue;
+    double *m = X + b * N2;
+    const double avg = 0.5 * (m[i * N + j] + m[j * N + i]);
+    m[i * N + j] = avg;
+    m[j * N + i] = avg;
+  }
+}
+}  // namespace
+
+gf2_status gf2_symmetrize(gf2_ctx *ctx, double *d_X, int count) {
+  const long long total = (long long)count * ctx->N * ctx->N;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 16LL * ctx->num_sms);
+  symmetrize_kernel<<<std::max(blocks, 1), 256, 0, ctx->stream>>>(ctx->N, count, d_X);
+  GF2_CK_LAUNCH(ctx, "symmetrize_kernel");
+  return GF2_OK;
+}

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(192, 1)
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      const int cp = u / NP, l = u % NP;
+      const int npairs = n_units / NP, l = u / npairs, cp = u % npairs;
       for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
         const int s = g % S;
         if (g >= S && !tc::mbar_wait(&a_empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(192, 1)
     int grp = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      const int cp = u / NP;
+      const int cp = u % (n_units / NP);
       float hi[64], lo[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.f;
@@ -409,6 +409,12 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---------------------------------------------------------------------------
 // stages 1+2 fused: T2[c][i][q][l][n] = sum_{m,k} G[m][n] v[i][m][q][k] G[k][l]
+//
+// Unit = (tau pair, i, q pair).  MMA1 covers both time points at once: its B
+// operand stacks G(tau_a)^T and G(tau_b)^T (N = 128), so D1 holds
+// [(m,q), (s,l)] for s = 0, 1.  Each half becomes one job for epilogue 1
+// (D1 -> A2 smem, MN-major) and MMA2 (N = 64, one time point).
+// TMEM: D1 buffers at columns 0 and 128 (128 wide), D2 buffers at 256, 320.
 // ---------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(320, 1)
@@ -417,10 +423,11 @@ __global__ void __launch_bounds__(320, 1)
   constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
   constexpr int A2S = (T == 2) ? 2 : 1;  // buffered MMA2 operands
   constexpr uint32_t A1_STAGE = T * TILE128, G_SET = 2 * T * TILE64, A2_BUF = T * TILE128;
+  constexpr uint32_t kIdescKK128 = tc::idesc_bf16(128, 128, 0, 0);
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *sA1 = smem;
-  uint8_t *sG = sA1 + 2 * A1_STAGE;
+  uint8_t *sG = sA1 + 2 * A1_STAGE;  // per set: [t][s][64][64]
   uint8_t *sA2 = sG + GS * G_SET;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sA2 + A2S * A2_BUF);
   uint64_t *a1_full = bar, *a1_empty = bar + 2, *g_full = bar + 4, *g_empty = bar + 6;
@@ -447,10 +454,10 @@ __global__ void __launch_bounds__(320, 1)
     tc::prefetch_tmap(&map_v);
     tc::prefetch_tmap(&map_g);
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, 256);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;  // D1 buffers at columns 0, 64; D2 at 128, 192
+  const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
   const size_t plane = (size_t)C * NP * NP * NP * NP;
 
@@ -462,9 +469,9 @@ __global__ void __launch_bounds__(320, 1)
         const int gs = gcount % GS;
         if (gcount >= GS && !tc::mbar_wait(&g_empty[gs], ((gcount / GS) - 1) & 1, abort)) { raise_abort(abort, err); break; }
         tc::mbar_arrive_expect_tx(&g_full[gs], G_SET);
-        for (int s = 0; s < 2; ++s)
-          for (int t = 0; t < T; ++t)
-            tc::tma_load_3d(sG + gs * G_SET + (s * T + t) * TILE64, &map_g, &g_full[gs], 0, 0,
+        for (int t = 0; t < T; ++t)
+          for (int s = 0; s < 2; ++s)
+            tc::tma_load_3d(sG + gs * G_SET + (t * 2 + s) * TILE64, &map_g, &g_full[gs], 0, 0,
                             t * C + 2 * cp + s);
         cur_cp = cp;
         ++gcount;
@@ -477,21 +484,24 @@ __global__ void __launch_bounds__(320, 1)
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_cp = -1, gcount = 0, gs = 0;
-    int pend = -1, pend_gs = 0, pend_s = 0;  // job whose MMA2 is not yet issued
+    int pend_u = -1, pend_gs = 0;  // unit whose two MMA2 jobs are not yet issued
     bool ok = true;
-    auto issue_mma2 = [&](int jj, int jgs, int js) -> bool {
-      const int ab = jj % A2S, db = jj & 1;
+    auto issue_mma2 = [&](int jj, int jgs) -> bool {
+      const int ab = jj % A2S, db = jj & 1, js = jj & 1;
       if (!tc::mbar_wait(&a2_full[ab], (jj / A2S) & 1, abort)) return false;
       if (jj >= 2 && !tc::mbar_wait(&d2_empty[db], ((jj >> 1) - 1) & 1, abort)) return false;
       tc::tc_fence_after();
-      const uint32_t a0 = tc::smem_u32(sA2 + ab * A2_BUF);
-      const uint32_t b0 = tc::smem_u32(sG + jgs * G_SET + js * T * TILE64);
+      const uint64_t a0 = tc::smem_desc(tc::smem_u32(sA2 + ab * A2_BUF), TILE64, 1024);
+      const uint64_t b0 = tc::smem_desc(tc::smem_u32(sG + jgs * G_SET + js * TILE64), 16, 1024);
+#pragma unroll
       for (int pr = 0; pr < Products<T>::n; ++pr) {
         const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+#pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 2048, TILE64, 1024);
-          const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
-          tc::mma_bf16(tmem + 128 + db * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
+          // descriptors advance in 16-byte units: A by 2048 B (16 K rows), B by 32 B
+          const uint64_t ad = a0 + (uint64_t)((ta * TILE128 + kk * 2048) >> 4);
+          const uint64_t bd = b0 + (uint64_t)((tb * 2 * TILE64 + kk * 32) >> 4);
+          tc::mma_bf16(tmem + 256 + db * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
         }
       }
       tc::mma_commit(&a2_empty[ab]);
@@ -501,9 +511,13 @@ __global__ void __launch_bounds__(320, 1)
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
       const int cp = u / (NP * 32);
       if (cp != cur_cp) {
-        if (pend >= 0) {  // finish the previous pair before its G set can be recycled
-          if (!issue_mma2(pend, pend_gs, pend_s)) { raise_abort(abort, err); ok = false; break; }
-          pend = -1;
+        if (pend_u >= 0) {  // finish the previous pair before its G set can be recycled
+          if (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)) {
+            raise_abort(abort, err);
+            ok = false;
+            break;
+          }
+          pend_u = -1;
           tc::mma_commit(&g_empty[gs]);
         }
         gs = gcount % GS;
@@ -511,52 +525,58 @@ __global__ void __launch_bounds__(320, 1)
         cur_cp = cp;
         ++gcount;
       }
-      const int st = it & 1;
+      const int st = it & 1, b = it & 1;
       if (!tc::mbar_wait(&a1_full[st], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-      for (int s = 0; s < 2; ++s) {
-        const int j = 2 * it + s, b = j & 1;
-        if (j >= 2 && !tc::mbar_wait(&d1_empty[b], ((j >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-        tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA1 + st * A1_STAGE);
-        const uint32_t b0 = tc::smem_u32(sG + gs * G_SET + s * T * TILE64);
-        for (int pr = 0; pr < Products<T>::n; ++pr) {
-          const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 32, 16, 1024);
-            const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
-            tc::mma_bf16(tmem + b * 64, ad, bd, kIdescKK, (pr | kk) ? 1u : 0u);
-          }
+      if (it >= 2 && !tc::mbar_wait(&d1_empty[b], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+      tc::tc_fence_after();
+      const uint64_t a0 = tc::smem_desc(tc::smem_u32(sA1 + st * A1_STAGE), 16, 1024);
+      const uint64_t b0 = tc::smem_desc(tc::smem_u32(sG + gs * G_SET), 16, 1024);
+#pragma unroll
+      for (int pr = 0; pr < Products<T>::n; ++pr) {
+        const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = a0 + (uint64_t)((ta * TILE128 + kk * 32) >> 4);
+          const uint64_t bd = b0 + (uint64_t)((tb * 2 * TILE64 + kk * 32) >> 4);
+          tc::mma_bf16(tmem + b * 128, ad, bd, kIdescKK128, (pr | kk) ? 1u : 0u);
         }
-        tc::mma_commit(&d1_full[b]);
-        if (s == 1) tc::mma_commit(&a1_empty[st]);
-        if (pend >= 0) {
-          if (!issue_mma2(pend, pend_gs, pend_s)) { raise_abort(abort, err); ok = false; break; }
-        }
-        pend = j;
-        pend_gs = gs;
-        pend_s = s;
       }
+      tc::mma_commit(&d1_full[b]);
+      tc::mma_commit(&a1_empty[st]);
+      if (pend_u >= 0) {
+        if (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)) {
+          raise_abort(abort, err);
+          ok = false;
+          break;
+        }
+      }
+      pend_u = it;
+      pend_gs = gs;
     }
-    if (ok && pend >= 0 && !issue_mma2(pend, pend_gs, pend_s)) raise_abort(abort, err);
+    if (ok && pend_u >= 0 && (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)))
+      raise_abort(abort, err);
   } else if (warp >= 2 && warp < 6) {
-    // epilogue 1: D1[(m,q), l] -> A2[(q,l), m] (MN-major, 128-byte swizzle)
+    // epilogue 1: D1[(m,q), (s,l)] -> A2_j[(q,l), m] (MN-major, 128-byte swizzle), j = 2 it + s
     const int wq = warp & 3, row = wq * 32 + lane;
     const int m = row >> 1, ql = row & 1;
-    int j = 0;
+    int it = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      for (int s = 0; s < 2; ++s, ++j) {
-        const int b = j & 1;
-        if (!tc::mbar_wait(&d1_full[b], (j >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-        tc::tc_fence_after();
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+      const int b = it & 1;
+      if (!tc::mbar_wait(&d1_full[b], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+      tc::tc_fence_after();
+      for (int s = 0; s < 2; ++s) {
+        const int j = 2 * it + s;
         float v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + b * 64;
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + b * 128 + s * 64;
         tc::tmem_ld_32x32b_x32(taddr, v);
         tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
         tc::tmem_ld_wait();
-        tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&d1_empty[b]);
+        if (s == 1) {
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&d1_empty[b]);
+        }
         const int ab = j % A2S;
         if (j >= A2S && !tc::mbar_wait(&a2_empty[ab], ((j / A2S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         uint8_t *dst = sA2 + ab * A2_BUF + ql * TILE64 + m * 128;
@@ -594,7 +614,7 @@ __global__ void __launch_bounds__(320, 1)
         if (!tc::mbar_wait(&d2_full[b], (j >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
         float v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + 128 + b * 64;
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + 256 + b * 64;
         tc::tmem_ld_32x32b_x32(taddr, v);
         tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
         tc::tmem_ld_wait();
@@ -610,7 +630,7 @@ __global__ void __launch_bounds__(320, 1)
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 256);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -888,6 +908,9 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, doub
                                  : run_chunks<3>(ctx, s, G_use, k0, count, out_use);
   if (st != GF2_OK) return st;
   if (ctx->d_Shalf && (st = gf2_orth_sigma_to_ao(ctx, out_use, count, d_out)) != GF2_OK) return st;
+  // Eq. Sigma is symmetric; the two triangles carry independent rounding of the
+  // split arithmetic, and their average is the better estimate
+  if ((st = gf2_symmetrize(ctx, d_out, count)) != GF2_OK) return st;
   int flag = 0;
   GF2_CK(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));

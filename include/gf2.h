@@ -147,8 +147,9 @@ gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_momen
 
 /* Step 2.a: find mu with Tr(P(mu) S) = n_elec to |error| <= tol, P(mu) from
  * Eq. GF and gf2_density.  Bracketing search started at *mu_inout (expanded
- * outward until it brackets), then Illinois false position with bisection
- * safeguards; at most max_iter evaluations (GF2_ERR_NOT_CONVERGED beyond).
+ * outward until it brackets), then Brent's method (inverse quadratic
+ * interpolation with bisection safeguards); at most max_iter evaluations
+ * (GF2_ERR_NOT_CONVERGED beyond).
  * On success *mu_inout = mu, d_G_iw and d_P hold G(i w) and P at that mu,
  * *n_eval (if not NULL) = number of Dyson evaluations.  Synchronizes. */
 gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,

@@ -471,25 +471,58 @@ extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const doubl
       hi = lo; fhi = flo; step *= 2.0; lo -= step;
     }
   }
-  // Illinois false position, bisecting whenever the secant point is unusable
-  int side = 0;
-  double last = mu0;
+  // Brent's method on the bracket: inverse quadratic interpolation or secant
+  // steps, falling back to bisection whenever they would not shrink it enough
+  double a = lo, fa = flo, b = hi, fb = fhi;
+  if (fabs(fa) < fabs(fb)) {
+    std::swap(a, b);
+    std::swap(fa, fb);
+  }
+  double c = a, fc = fa, d = b - a, e = d;
+  double last = b;
   while (evals < max_iter) {
-    double mu = (lo * fhi - hi * flo) / (fhi - flo);
-    if (!(mu > lo && mu < hi) || (hi - lo) < 1e-15 * std::max(1.0, fabs(mu))) mu = 0.5 * (lo + hi);
-    double f;
-    if ((st = count(mu, &f)) != GF2_OK) return st;
-    last = mu;
-    if (fabs(f) <= tol) return done(mu);
-    if (f < 0.0) {
-      lo = mu; flo = f;
-      if (side == -1) fhi *= 0.5;
-      side = -1;
-    } else {
-      hi = mu; fhi = f;
-      if (side == 1) flo *= 0.5;
-      side = 1;
+    if ((fb > 0.0) == (fc > 0.0)) {
+      c = a;
+      fc = fa;
+      d = e = b - a;
     }
+    if (fabs(fc) < fabs(fb)) {
+      a = b; b = c; c = a;
+      fa = fb; fb = fc; fc = fa;
+    }
+    const double tol1 = 2.0 * 2.2e-16 * fabs(b) + 1e-16;
+    const double xm = 0.5 * (c - b);
+    if (fabs(xm) <= tol1) break;  // bracket collapsed without reaching tol
+    if (fabs(e) >= tol1 && fabs(fa) > fabs(fb)) {
+      const double sq = fb / fa;
+      double p, q;
+      if (a == c) {
+        p = 2.0 * xm * sq;
+        q = 1.0 - sq;
+      } else {
+        const double qq = fa / fc, r = fb / fc;
+        p = sq * (2.0 * xm * qq * (qq - r) - (b - a) * (r - 1.0));
+        q = (qq - 1.0) * (r - 1.0) * (sq - 1.0);
+      }
+      if (p > 0.0) q = -q;
+      p = fabs(p);
+      if (2.0 * p < std::min(3.0 * xm * q - fabs(tol1 * q), fabs(e * q))) {
+        e = d;
+        d = p / q;
+      } else {
+        d = xm;
+        e = d;
+      }
+    } else {
+      d = xm;
+      e = d;
+    }
+    a = b;
+    fa = fb;
+    b += (fabs(d) > tol1) ? d : (xm > 0.0 ? tol1 : -tol1);
+    if ((st = count(b, &fb)) != GF2_OK) return st;
+    last = b;
+    if (fabs(fb) <= tol) return done(b);
   }
   *mu_inout = last;
   if (n_eval) *n_eval = evals;

@@ -421,13 +421,14 @@ __global__ void __launch_bounds__(320, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
                     __nv_bfloat16 *__restrict__ t2, int C, int n_units, int *err) {
   constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
-  constexpr int A2S = (T == 2) ? 2 : 1;  // buffered MMA2 operands
+  constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
+  constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
   constexpr uint32_t A1_STAGE = T * TILE128, G_SET = 2 * T * TILE64, A2_BUF = T * TILE128;
   constexpr uint32_t kIdescKK128 = tc::idesc_bf16(128, 128, 0, 0);
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *sA1 = smem;
-  uint8_t *sG = sA1 + 2 * A1_STAGE;  // per set: [t][s][64][64]
+  uint8_t *sG = sA1 + A1S * A1_STAGE;  // per set: [t][s][64][64]
   uint8_t *sA2 = sG + GS * G_SET;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sA2 + A2S * A2_BUF);
   uint64_t *a1_full = bar, *a1_empty = bar + 2, *g_full = bar + 4, *g_empty = bar + 6;
@@ -476,8 +477,8 @@ __global__ void __launch_bounds__(320, 1)
         cur_cp = cp;
         ++gcount;
       }
-      const int st = it & 1;
-      if (it >= 2 && !tc::mbar_wait(&a1_empty[st], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      const int st = it % A1S;
+      if (it >= A1S && !tc::mbar_wait(&a1_empty[st], ((it / A1S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::mbar_arrive_expect_tx(&a1_full[st], A1_STAGE);
       for (int t = 0; t < T; ++t)
         tc::tma_load_5d(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 2 * qp, 0, i, t);
@@ -525,8 +526,8 @@ __global__ void __launch_bounds__(320, 1)
         cur_cp = cp;
         ++gcount;
       }
-      const int st = it & 1, b = it & 1;
-      if (!tc::mbar_wait(&a1_full[st], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+      const int st = it % A1S, b = it & 1;
+      if (!tc::mbar_wait(&a1_full[st], (it / A1S) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
       if (it >= 2 && !tc::mbar_wait(&d1_empty[b], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
       tc::tc_fence_after();
       const uint64_t a0 = tc::smem_desc(tc::smem_u32(sA1 + st * A1_STAGE), 16, 1024);
@@ -741,8 +742,8 @@ constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
 
 template <int T>
 size_t smem_sandwich() {
-  const int GS = (T == 2) ? 2 : 1, A2S = (T == 2) ? 2 : 1;
-  return 1024 + 2 * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
+  const int GS = (T == 2) ? 2 : 1, A1S = (T == 2) ? 2 : 1, A2S = 2;
+  return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
 }
 template <int T>
 size_t smem_xform() { return 1024 + ((T == 2) ? 4 : 3) * T * TILE128 + 2 * T * TILE64 + 256; }

@@ -10,19 +10,26 @@
 //             points.  MMA1  D1[(m,q), l]   = sum_k V[(m,q),k] G[k,l]
 //             (TMEM) -> split by four epilogue warps into an MN-major smem
 //             operand A2[(q,l), m] -> MMA2  D2[(q,l), n] = sum_m A2 G[m,n]
-//             -> four more warps split and store T2[tau][i][q][l][n].
+//             -> four more warps store T2[tau][i][q][l][n] in FP32.
 //  xform      stage 3.  D3[(l,n), p] = sum_q T2[tau][i][q][(l,n)] Gbar[p,q]
-//             with T2 read MN-major straight from HBM by TMA;
-//             stores T3[tau][i][l][n][p].
+//             with the FP32 T2 tile read by TMA and split on chip into the
+//             MN-major bf16 operand; stores T3[tau][i][l][n][p] in FP32.
 //  contract   stage 4.  Sigma[(tau,i), j] -= sum_K T3[(tau,i), K] Wt4[j, K],
-//             K = (l,n,p) of length NP^3, rows = two time points x 64 i.
-//             Split over K in slices of NP^2 (FP32 accumulation in TMEM per
-//             slice) and reduced into the FP64 output with atomics.
+//             K = (l,n,p) of length NP^3, rows = two time points x 64 i;
+//             T3 tiles are split on chip like T2.  Split over K in slices of
+//             NP^2 (FP32 accumulation in TMEM per slice) and reduced into the
+//             FP64 output with atomics.
+//
+// The intermediates T2 and T3 live in HBM as FP32 (4 bytes per value instead
+// of 2T for stored bf16 terms).  T bf16 terms of an FP32 value are formed by
+// the same rounding on either side of the store, so the operands the tensor
+// cores see are the same as if the terms had been stored.
 //
 // All three are persistent, warp-specialised: one TMA producer thread, one
-// MMA-issuing thread, and epilogue warpgroups that own the TMEM lane quarters
-// (warp w reads lanes 32*(w%4) .. +31).  Waits are bounded; a timeout raises
-// the context error word and the kernel drains and exits.
+// MMA-issuing thread, converter warps where an FP32 tile is split, and
+// epilogue warps that own the TMEM lane quarters (warp w reads lanes
+// 32*(w%4) .. +31).  Waits are bounded; a timeout raises the context error
+// word and the kernel drains and exits.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -68,26 +75,43 @@ __device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
   atomicExch(err, kErrTimeout);
 }
 
-// write 64 consecutive fp32 values, split into T bf16 terms, as one 128-byte
-// row per term: dst[t * plane + 0..63]
+// write 64 consecutive fp32 values as one 256-byte row
+__device__ __forceinline__ void store_row_f32(float *dst, const float *v) {
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    reinterpret_cast<float4 *>(dst)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
+// split four consecutive fp32 values into T bf16 terms; term t goes to the
+// 8 bytes at dst + t * plane (the operand planes of one tile).  Pairs are
+// rounded together (cvt.rn.bf16x2), so each term is the same round-to-nearest
+// split as tc::split_f32, and every residual is exact in fp32.
 template <int T>
-__device__ __forceinline__ void store_row_split(__nv_bfloat16 *dst, size_t plane, const float *v) {
+__device__ __forceinline__ void split4_store(float4 x, uint8_t *dst, uint32_t plane) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    __nv_bfloat16 p[8][T];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) tc::split_f32<T>(v[8 * c + e], p[e]);
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-      uint4 w;
-      w.x = tc::pack2(p[0][t], p[1][t]);
-      w.y = tc::pack2(p[2][t], p[3][t]);
-      w.z = tc::pack2(p[4][t], p[5][t]);
-      w.w = tc::pack2(p[6][t], p[7][t]);
-      *reinterpret_cast<uint4 *>(dst + t * plane + 8 * c) = w;
+  for (int t = 0; t < T; ++t) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
+    *reinterpret_cast<uint2 *>(dst + t * plane) =
+        make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
+    if (t + 1 < T) {
+      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+      x.x -= fa.x;
+      x.y -= fa.y;
+      x.z -= fb.x;
+      x.w -= fb.y;
     }
   }
 }
+
+// The converter warps of the xform and contract kernels turn an FP32 tile of
+// 128 x 64 values into T bf16 planes in place: the planes occupy the first
+// T * 16 KB of a stage and the TMA lands the FP32 tile in its last 32 KB.
+// Each of the four converter warps first reads its 16 rows of 16-byte chunks
+// into registers; after all four have read (a bounded mbarrier, so that a
+// timed-out pipeline cannot leave a warp waiting for ever) they write.
+constexpr uint32_t kF32Tile = 128 * NP * 4;  // 32 KB
+template <int T>
+__host__ __device__ constexpr uint32_t f32_offset() { return T * TILE128 - kF32Tile; }
 
 // ---------------------------------------------------------------------------
 // splitting of the FP64 inputs
@@ -156,11 +180,17 @@ __global__ void split_g_kernel(int N, int M, int k0, int count, int C, const dou
 
 // ---------------------------------------------------------------------------
 // stage 3: T3[c][i][l][n][p] = sum_q Gbar_c[p][q] T2[c][i][q][l][n]
+//
+// Unit (c, i, 128 rows of (l,n)).  The FP32 tile T2[c][i][q][(l,n)] arrives by
+// TMA; four converter warps split it in place into T bf16 planes laid out as
+// the MN-major, 128-byte-swizzled A operand; the MMA warp multiplies by the
+// Gbar planes; four epilogue warps store the FP32 rows T3[c][i][(l,n)][p].
+// 320 threads: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue, warps 6-9 convert.
 // ---------------------------------------------------------------------------
 template <int T>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
-                 __nv_bfloat16 *__restrict__ t3, int C, int n_units, int *err) {
+                 float *__restrict__ t3, int C, int n_units, int *err) {
   constexpr int S = (T == 2) ? 4 : 3;
   constexpr uint32_t A_STAGE = T * TILE128, B_SET = T * TILE64;
   extern __shared__ uint8_t smem_raw[];
@@ -168,15 +198,17 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t *sA = smem;
   uint8_t *sB = sA + S * A_STAGE;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * B_SET);
-  uint64_t *a_full = bar, *a_empty = bar + S, *b_full = bar + 2 * S, *b_empty = bar + 2 * S + 2;
-  uint64_t *d_full = bar + 2 * S + 4, *d_empty = bar + 2 * S + 6;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * S + 8);
+  uint64_t *full = bar, *rd = bar + S, *conv = bar + 2 * S, *empty = bar + 3 * S;
+  uint64_t *b_full = bar + 4 * S, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 8);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&a_full[s], 1);
-      tc::mbar_init(&a_empty[s], 1);
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&rd[s], 4);
+      tc::mbar_init(&conv[s], 4);
+      tc::mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&b_full[s], 1);
@@ -194,7 +226,6 @@ __global__ void __launch_bounds__(192, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
-  const size_t plane = (size_t)C * NP * NP * NP * NP;
 
   if (warp == 0 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0;
@@ -210,12 +241,9 @@ __global__ void __launch_bounds__(192, 1)
         ++gcount;
       }
       const int s = it % S;
-      if (it >= S && !tc::mbar_wait(&a_empty[s], ((it / S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
-      tc::mbar_arrive_expect_tx(&a_full[s], A_STAGE);
-      for (int t = 0; t < T; ++t)
-        for (int h = 0; h < 2; ++h)
-          tc::tma_load_4d(sA + s * A_STAGE + t * TILE128 + h * TILE64, &map_t2, &a_full[s], mt * 128 + h * 64, 0,
-                          c * NP + i, t);
+      if (it >= S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::mbar_arrive_expect_tx(&full[s], kF32Tile);
+      tc::tma_load_3d(sA + s * A_STAGE + f32_offset<T>(), &map_t2, &full[s], mt * 128, 0, c * NP + i);
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0, gs = 0;
@@ -229,7 +257,7 @@ __global__ void __launch_bounds__(192, 1)
         ++gcount;
       }
       const int s = it % S, d = it & 1;
-      if (!tc::mbar_wait(&a_full[s], (it / S) & 1, abort)) { raise_abort(abort, err); break; }
+      if (!tc::mbar_wait(&conv[s], (it / S) & 1, abort)) { raise_abort(abort, err); break; }
       if (it >= 2 && !tc::mbar_wait(&d_empty[d], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::tc_fence_after();
       const uint32_t a0 = tc::smem_u32(sA + s * A_STAGE), b0 = tc::smem_u32(sB + gs * B_SET);
@@ -241,10 +269,10 @@ __global__ void __launch_bounds__(192, 1)
           tc::mma_bf16(tmem + d * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
         }
       }
-      tc::mma_commit(&a_empty[s]);
+      tc::mma_commit(&empty[s]);
       tc::mma_commit(&d_full[d]);
     }
-  } else if (warp >= 2) {
+  } else if (warp >= 2 && warp < 6) {
     const int wq = warp & 3, row = wq * 32 + lane;
     int it = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
@@ -261,7 +289,35 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&d_empty[d]);
       const size_t off = (((size_t)c * NP + i) * (NP * NP) + (size_t)mt * 128 + row) * NP;
-      store_row_split<T>(t3 + off, plane, v);
+      store_row_f32(t3 + off, v);
+    }
+  } else if (warp >= 6) {
+    // converter: F[q][m] (fp32, m = 128 rows of (l,n)) -> A planes [h][q][64 m],
+    // 16-byte chunk (m % 64) / 8 stored at chunk ^ (q % 8).  Lane owns
+    // m = 4 lane .. +3; warp cw takes q = cw, cw + 4, ...
+    const int cw = warp - 6, h = lane >> 4, cc = (lane & 15) >> 1, half = lane & 1;
+    int it = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+      const int s = it % S;
+      const uint32_t par = (it / S) & 1;
+      if (!tc::mbar_wait(&full[s], par, abort)) { raise_abort(abort, err); break; }
+      uint8_t *stage = sA + s * A_STAGE;
+      float4 x[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        x[r] = *reinterpret_cast<const float4 *>(stage + f32_offset<T>() + (4 * r + cw) * 512 + lane * 16);
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&rd[s]);
+      if (!tc::mbar_wait(&rd[s], par, abort)) { raise_abort(abort, err); break; }
+      uint8_t *dst = stage + h * TILE64 + half * 8;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int q = 4 * r + cw;
+        split4_store<T>(x[r], dst + q * 128 + ((cc ^ (q & 7)) << 4), TILE128);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[s]);
     }
   }
   __syncthreads();
@@ -289,28 +345,31 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 }
 
 template <int T, int KSUB>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
                     double *__restrict__ out, int N, int count, int C, int n_units, int *err) {
   constexpr int S = (T == 2) ? 4 : 3;
   constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
   constexpr int NGROUP = KSTEPS / KSUB;
-  constexpr uint32_t STAGE = T * (TILE128 + TILE64);
+  constexpr uint32_t STAGE = T * (TILE128 + TILE64);  // A planes (FP32 tile lands at the end), W planes
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S * STAGE);
-  uint64_t *a_full = bar, *a_empty = bar + S, *d_full = bar + 2 * S, *d_empty = bar + 2 * S + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2 * S + 4);
+  uint64_t *full = bar, *rd = bar + S, *conv = bar + 2 * S, *empty = bar + 3 * S;
+  uint64_t *d_full = bar + 4 * S, *d_empty = d_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_full + 4);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&a_full[s], 1);
-      tc::mbar_init(&a_empty[s], 1);
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&rd[s], 4);
+      tc::mbar_init(&conv[s], 4);
+      tc::mbar_init(&empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&d_full[s], 1);
-      tc::mbar_init(&d_empty[s], 4);
+      tc::mbar_init(&d_empty[s], 8);
     }
     tc::fence_barrier_init();
     s_abort = 0;
@@ -322,22 +381,22 @@ __global__ void __launch_bounds__(192, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
+  const int npairs = n_units / NP;
 
   if (warp == 0 && lane == 0) {
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      const int npairs = n_units / NP, l = u / npairs, cp = u % npairs;
+      const int l = u / npairs, cp = u % npairs;
       for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
-        const int s = g % S;
-        if (g >= S && !tc::mbar_wait(&a_empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-        tc::mbar_arrive_expect_tx(&a_full[s], STAGE);
         const int k0 = l * NP * NP + ks * NP;
+        const int s = g % S;
+        if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         uint8_t *st = smem + s * STAGE;
-        for (int t = 0; t < T; ++t) {
-          tc::tma_load_3d(st + t * TILE128, &map_t3, &a_full[s], k0, cp * 128, t);
-          tc::tma_load_3d(st + T * TILE128 + t * TILE64, &map_w, &a_full[s], k0, 0, t);
-        }
+        tc::mbar_arrive_expect_tx(&full[s], kF32Tile + T * TILE64);
+        tc::tma_load_3d(st + f32_offset<T>(), &map_t3, &full[s], k0, cp * 128, 0);
+        for (int t = 0; t < T; ++t)
+          tc::tma_load_3d(st + T * TILE128 + t * TILE64, &map_w, &full[s], k0, 0, t);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -350,7 +409,7 @@ __global__ void __launch_bounds__(192, 1)
         tc::tc_fence_after();
         for (int kq = 0; kq < KSUB; ++kq, ++g) {
           const int s = g % S;
-          if (!tc::mbar_wait(&a_full[s], (g / S) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+          if (!tc::mbar_wait(&conv[s], (g / S) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
           tc::tc_fence_after();
           const uint32_t base = tc::smem_u32(smem + s * STAGE);
           for (int pr = 0; pr < Products<T>::n; ++pr) {
@@ -361,42 +420,73 @@ __global__ void __launch_bounds__(192, 1)
               tc::mma_bf16(tmem + d * 64, ad, bd, kIdescKK, (kq | pr | kk) ? 1u : 0u);
             }
           }
-          tc::mma_commit(&a_empty[s]);
+          tc::mma_commit(&empty[s]);
         }
         if (ok) tc::mma_commit(&d_full[d]);
       }
     }
-  } else if (warp >= 2) {
-    const int wq = warp & 3, row = wq * 32 + lane;
+  } else if (warp >= 2 && warp < 10) {
+    // epilogue: warp w reads TMEM lane quarter w % 4, columns 32 * ((w - 2) / 4) .. +31
+    const int wq = warp & 3, row = wq * 32 + lane, col = 32 * ((warp - 2) >> 2);
     int grp = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-      const int cp = u % (n_units / NP);
-      float hi[64], lo[64];
+      const int cp = u % npairs;
+      float hi[32], lo[32];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) hi[j] = lo[j] = 0.f;
+      for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
       for (int gi = 0; gi < NGROUP; ++gi, ++grp) {
         const int d = grp & 1;
         if (!tc::mbar_wait(&d_full[d], (grp >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
-        float v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + d * 64;
-        tc::tmem_ld_32x32b_x32(taddr, v);
-        tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+        float v[32];
+        tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(wq * 32) << 16) + d * 64 + col, v);
         tc::tmem_ld_wait();
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&d_empty[d]);
 #pragma unroll
-        for (int j = 0; j < 64; ++j) two_sum_acc(hi[j], lo[j], v[j]);
+        for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], v[j]);
       }
       if (!ok) break;
       const int c = 2 * cp + row / NP, i = row % NP;
       if (c < count && i < N) {
-        double *o = out + ((size_t)c * N + i) * N;
+        double *o = out + ((size_t)c * N + i) * N + col;
 #pragma unroll
-        for (int j = 0; j < 64; ++j)
-          if (j < N) atomicAdd(o + j, -((double)hi[j] + (double)lo[j]));
+        for (int j = 0; j < 32; ++j)
+          if (col + j < N) atomicAdd(o + j, -((double)hi[j] + (double)lo[j]));
+      }
+    }
+  } else if (warp >= 10) {
+    // converter: F[r][k] (fp32, 128 rows x 64 k) -> A planes [r][64 k], K-major,
+    // 16-byte chunk k / 8 stored at chunk ^ (r % 8).  A warp pass covers rows
+    // 2 rp, 2 rp + 1 (rp = cw, cw + 4, ...); lane owns k = 4 (lane % 16) .. +3
+    // of row 2 rp + lane / 16.
+    const int cw = warp - 10, rsub = lane >> 4, cc = (lane & 15) >> 1, half = lane & 1;
+    int g = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
+        const int s = g % S;
+        const uint32_t par = (g / S) & 1;
+        if (!tc::mbar_wait(&full[s], par, abort)) { raise_abort(abort, err); ok = false; break; }
+        uint8_t *stage = smem + s * STAGE;
+        float4 x[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          x[r] = *reinterpret_cast<const float4 *>(stage + f32_offset<T>() + (4 * r + cw) * 512 + lane * 16);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&rd[s]);
+        if (!tc::mbar_wait(&rd[s], par, abort)) { raise_abort(abort, err); ok = false; break; }
+        uint8_t *dst = stage + half * 8;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int row = 2 * (4 * r + cw) + rsub;
+          split4_store<T>(x[r], dst + row * 128 + ((cc ^ (row & 7)) << 4), TILE128);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[s]);
       }
     }
   }
@@ -419,7 +509,7 @@ __global__ void __launch_bounds__(192, 1)
 template <int T>
 __global__ void __launch_bounds__(320, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
-                    __nv_bfloat16 *__restrict__ t2, int C, int n_units, int *err) {
+                    float *__restrict__ t2, int C, int n_units, int *err) {
   constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
   constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
   constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
@@ -460,7 +550,6 @@ __global__ void __launch_bounds__(320, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
-  const size_t plane = (size_t)C * NP * NP * NP * NP;
 
   if (warp == 0 && lane == 0) {
     int it = 0, cur_cp = -1, gcount = 0;
@@ -624,7 +713,7 @@ __global__ void __launch_bounds__(320, 1)
         if (lane == 0) tc::mbar_arrive(&d2_empty[b]);
         const int c = 2 * cp + s, q = 2 * qp + ql;
         const size_t off = ((((size_t)c * NP + i) * NP + q) * NP + l) * NP;
-        store_row_split<T>(t2 + off, plane, v);
+        store_row_f32(t2 + off, v);
       }
     }
   }
@@ -719,22 +808,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// bf16 operand tiles use the 128-byte swizzle of the MMA layouts; fp32 tiles
+// (split on chip) are plain row-major
 bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-              const uint32_t *box) {
+              const uint32_t *box, bool fp32 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void *>(base),
-                  reinterpret_cast<const cuuint64_t *>(dims), reinterpret_cast<const cuuint64_t *>(strides_bytes),
-                  reinterpret_cast<const cuuint32_t *>(box), es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank,
+                  const_cast<void *>(base), reinterpret_cast<const cuuint64_t *>(dims),
+                  reinterpret_cast<const cuuint64_t *>(strides_bytes), reinterpret_cast<const cuuint32_t *>(box), es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 struct TcState {
   int C = 0;
-  __nv_bfloat16 *Gs = nullptr, *T2 = nullptr, *T3 = nullptr;
+  __nv_bfloat16 *Gs = nullptr;
+  float *T2 = nullptr, *T3 = nullptr;  // FP32 intermediates, C * NP^4 each
   CUtensorMap map_v, map_g, map_t2, map_t3, map_w;
 };
 
@@ -770,11 +862,11 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
     GF2_PROF(ctx, GF2_K_XFORM,
-             (xform_kernel<T><<<std::min(u2, sms), 192, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->T3, C, u2, ctx->d_err)));
+             (xform_kernel<T><<<std::min(u2, sms), 320, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->T3, C, u2, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "xform_kernel");
     const int u3 = (ce / 2) * NP;
     GF2_PROF(ctx, GF2_K_CONTRACT,
-             (contract_kernel<T, kContractGroup><<<std::min(u3, sms), 192, sct, ctx->stream>>>(
+             (contract_kernel<T, kContractGroup><<<std::min(u3, sms), 448, sct, ctx->stream>>>(
                  s->map_t3, s->map_w, out, N, cnt, C, u3, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "contract_kernel");
   }
@@ -823,7 +915,7 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
   s->C = std::max(2, std::min(32, ((ctx->n_tau + 1) / 2) * 2));
   const int C = s->C;
   const size_t gbytes = (size_t)2 * TMAX * C * NP * NP * sizeof(__nv_bfloat16);
-  const size_t ibytes = (size_t)TMAX * C * kPlane4 * sizeof(__nv_bfloat16);
+  const size_t ibytes = (size_t)C * kPlane4 * sizeof(float);
   cudaError_t e = cudaMalloc(&s->Gs, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->T2, ibytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->T3, ibytes);
@@ -849,17 +941,17 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     uint32_t box[3] = {64, 64, 1};
     ok &= make_map(&s->map_g, s->Gs, 3, dims, str, box);
   }
-  {  // T2: dims ((l,n) 4096, q 64, (c,i) C*64, t), box (64, 64, 1, 1): MN-major tiles
-    uint64_t dims[4] = {NP * NP, NP, (uint64_t)C * NP, TMAX};
-    uint64_t str[3] = {NP * NP * 2, (uint64_t)NP * NP * NP * 2, (uint64_t)C * kPlane4 * 2};
-    uint32_t box[4] = {64, 64, 1, 1};
-    ok &= make_map(&s->map_t2, s->T2, 4, dims, str, box);
+  {  // T2 (fp32): dims ((l,n) 4096, q 64, (c,i) C*64), box (128, 64, 1) -> F[q][128 (l,n)]
+    uint64_t dims[3] = {NP * NP, NP, (uint64_t)C * NP};
+    uint64_t str[2] = {NP * NP * 4, (uint64_t)NP * NP * NP * 4};
+    uint32_t box[3] = {128, 64, 1};
+    ok &= make_map(&s->map_t2, s->T2, 3, dims, str, box, true);
   }
-  {  // T3: dims (K = NP^3, rows (c,i) C*64, t), box (64, 128, 1)
-    uint64_t dims[3] = {(uint64_t)NP * NP * NP, (uint64_t)C * NP, TMAX};
-    uint64_t str[2] = {(uint64_t)NP * NP * NP * 2, (uint64_t)C * kPlane4 * 2};
+  {  // T3 (fp32): dims (K = NP^3, rows (c,i) C*64, 1), box (64, 128, 1) -> F[row][64 k]
+    uint64_t dims[3] = {(uint64_t)NP * NP * NP, (uint64_t)C * NP, 1};
+    uint64_t str[2] = {(uint64_t)NP * NP * NP * 4, (uint64_t)C * kPlane4 * 4};
     uint32_t box[3] = {64, 128, 1};
-    ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box);
+    ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box, true);
   }
   {  // W: dims (K = NP^3, j 64, t), box (64, 64, 1)
     uint64_t dims[3] = {(uint64_t)NP * NP * NP, NP, TMAX};

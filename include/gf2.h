@@ -148,10 +148,15 @@ gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_momen
 /* Step 2.a: find mu with Tr(P(mu) S) = n_elec to |error| <= tol, P(mu) from
  * Eq. GF and gf2_density.  Bracketing search started at *mu_inout (expanded
  * outward until it brackets), then Brent's method (inverse quadratic
- * interpolation with bisection safeguards); at most max_iter evaluations
- * (GF2_ERR_NOT_CONVERGED beyond).
- * On success *mu_inout = mu, d_G_iw and d_P hold G(i w) and P at that mu,
- * *n_eval (if not NULL) = number of Dyson evaluations.  Synchronizes. */
+ * interpolation with bisection safeguards).  When n_iw >= 2048 a coarse stage
+ * runs first: the same search on the count from the lowest n_iw/8 frequencies
+ * plus the analytic tail (Dyson at an eighth of the cost), which places mu
+ * and the local slope dN/dmu; the full-frequency search then starts there
+ * with a first step of twice the Newton step.  Convergence is decided on the
+ * full count only.  At most max_iter full evaluations (GF2_ERR_NOT_CONVERGED
+ * beyond).  On success *mu_inout = mu, d_G_iw and d_P hold G(i w) and P at that
+ * mu from a full evaluation, *n_eval (if not NULL) = number of Dyson
+ * evaluations, coarse and full.  Synchronizes. */
 gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
                          const double *d_Sigma_iw, const double *d_sig12, double n_elec,
                          double tol, int max_iter, double *mu_inout, double *d_G_iw,

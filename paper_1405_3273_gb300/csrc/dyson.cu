@@ -339,14 +339,14 @@ gf2_status launch_moments(gf2_ctx *ctx, double mu, double *mom) {
   return GF2_OK;
 }
 
+// Dyson at the lowest nb frequencies (all of them when nb = n_iw)
 gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *F, const double *Sig,
-                        double *G) {
+                        double *G, int nb) {
   const int N = ctx->N;
   const int per = (N * (N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
   GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   const double2 *sg = reinterpret_cast<const double2 *>(Sig);
   double2 *gg = reinterpret_cast<double2 *>(G);
-  const int nb = ctx->n_iw;
   cudaStream_t st = ctx->stream;
   if (per <= 1) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
   else if (per <= 2) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
@@ -359,17 +359,19 @@ gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *
   return GF2_OK;
 }
 
-gf2_status launch_density(gf2_ctx *ctx, const double *G, const double *coef, double *P) {
+// density from the lowest n_f frequencies; resum holds the tail sums over the same range
+gf2_status launch_density(gf2_ctx *ctx, const double *G, const double *coef, double *P, int n_f,
+                          const double *resum) {
   const int N2 = ctx->N * ctx->N;
   const int chunk = 256;
-  const int nchunks = (ctx->n_iw + chunk - 1) / chunk;
+  const int nchunks = (n_f + chunk - 1) / chunk;
   dim3 grid((N2 + 127) / 128, nchunks);
   GF2_PROF(ctx, GF2_K_DENSITY,
-           (density_partial_kernel<<<grid, 128, 0, ctx->stream>>>(N2, ctx->n_iw, chunk,
+           (density_partial_kernel<<<grid, 128, 0, ctx->stream>>>(N2, n_f, chunk,
                                                                   reinterpret_cast<const double2 *>(G), ctx->d_red)));
   GF2_CK_LAUNCH(ctx, "density_partial_kernel");
   density_final_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(
-      N2, nchunks, ctx->beta, ctx->d_red, coef, ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M, P);
+      N2, nchunks, ctx->beta, ctx->d_red, coef, resum, ctx->d_tau_pole + 4 * (size_t)ctx->M, P);
   GF2_CK_LAUNCH(ctx, "density_final_kernel");
   return GF2_OK;
 }
@@ -397,7 +399,7 @@ extern "C" gf2_status gf2_dyson(gf2_ctx *ctx, double mu, const double *d_S, cons
   if (!ctx) return GF2_ERR_ARG;
   if (!d_S || !d_F || !d_G_iw) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_dyson: NULL pointer");
   if (!std::isfinite(mu)) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_dyson: mu not finite");
-  return launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw);
+  return launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw, ctx->n_iw);
 }
 
 extern "C" gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_moments, double *d_P) {
@@ -406,7 +408,7 @@ extern "C" gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const doub
   double *coef = slot(ctx, SL_COEF);
   gf2_status st = gf2_pole_coefficients(ctx, d_moments, coef);
   if (st != GF2_OK) return st;
-  return launch_density(ctx, d_G_iw, coef, d_P);
+  return launch_density(ctx, d_G_iw, coef, d_P, ctx->n_iw, ctx->d_pole_resum);
 }
 
 extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
@@ -423,12 +425,13 @@ extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const doubl
   if (st != GF2_OK) return st;
   double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
   int evals = 0;
-  auto count = [&](double mu, double *out) -> gf2_status {
+  // f(mu) = N(mu) - n_elec from the lowest nf frequencies (tail sums over the same range)
+  auto count = [&](double mu, int nf, const double *resum, double *out) -> gf2_status {
     gf2_status s;
     if ((s = launch_moments(ctx, mu, mom)) != GF2_OK) return s;
     if ((s = gf2_pole_coefficients(ctx, mom, coef)) != GF2_OK) return s;
-    if ((s = launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw)) != GF2_OK) return s;
-    if ((s = launch_density(ctx, d_G_iw, coef, d_P)) != GF2_OK) return s;
+    if ((s = launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw, nf)) != GF2_OK) return s;
+    if ((s = launch_density(ctx, d_G_iw, coef, d_P, nf, resum)) != GF2_OK) return s;
     trace_kernel<<<1, 256, 0, ctx->stream>>>(ctx->N, d_P, d_S, cnt);
     GF2_CK_LAUNCH(ctx, "trace_kernel");
     GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, cnt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -442,91 +445,145 @@ extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const doubl
     if (!std::isfinite(*out)) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: non-finite count");
     return GF2_OK;
   };
-  auto done = [&](double mu) {
-    *mu_inout = mu;
-    if (n_eval) *n_eval = evals;
-    return GF2_OK;
+  // Root of f from mu0: bracket outward (first step from the slope hint when
+  // there is one, else 0.05; doubling), then Brent's method.  *found tells
+  // whether |f| <= tol was reached; *mu_out is the last point evaluated and
+  // *slope the secant slope of the last two points (0 if unknown).
+  struct Result {
+    double mu = 0.0, slope = 0.0;
+    bool found = false;
   };
-  double mu0 = *mu_inout, f0;
-  if ((st = count(mu0, &f0)) != GF2_OK) return st;
-  if (fabs(f0) <= tol) return done(mu0);
-  // bracket: step outward, doubling
-  double lo, hi, flo, fhi, step = 0.05;
-  if (f0 < 0.0) {
-    lo = mu0; flo = f0; hi = mu0 + step;
-    for (;;) {
-      if (evals >= max_iter) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: no bracket");
-      if ((st = count(hi, &fhi)) != GF2_OK) return st;
-      if (fabs(fhi) <= tol) return done(hi);
-      if (fhi > 0.0) break;
-      lo = hi; flo = fhi; step *= 2.0; hi += step;
-    }
-  } else {
-    hi = mu0; fhi = f0; lo = mu0 - step;
-    for (;;) {
-      if (evals >= max_iter) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: no bracket");
-      if ((st = count(lo, &flo)) != GF2_OK) return st;
-      if (fabs(flo) <= tol) return done(lo);
-      if (flo < 0.0) break;
-      hi = lo; fhi = flo; step *= 2.0; lo -= step;
-    }
-  }
-  // Brent's method on the bracket: inverse quadratic interpolation or secant
-  // steps, falling back to bisection whenever they would not shrink it enough
-  double a = lo, fa = flo, b = hi, fb = fhi;
-  if (fabs(fa) < fabs(fb)) {
-    std::swap(a, b);
-    std::swap(fa, fb);
-  }
-  double c = a, fc = fa, d = b - a, e = d;
-  double last = b;
-  while (evals < max_iter) {
-    if ((fb > 0.0) == (fc > 0.0)) {
-      c = a;
-      fc = fa;
-      d = e = b - a;
-    }
-    if (fabs(fc) < fabs(fb)) {
-      a = b; b = c; c = a;
-      fa = fb; fb = fc; fc = fa;
-    }
-    const double tol1 = 2.0 * 2.2e-16 * fabs(b) + 1e-16;
-    const double xm = 0.5 * (c - b);
-    if (fabs(xm) <= tol1) break;  // bracket collapsed without reaching tol
-    if (fabs(e) >= tol1 && fabs(fa) > fabs(fb)) {
-      const double sq = fb / fa;
-      double p, q;
-      if (a == c) {
-        p = 2.0 * xm * sq;
-        q = 1.0 - sq;
-      } else {
-        const double qq = fa / fc, r = fb / fc;
-        p = sq * (2.0 * xm * qq * (qq - r) - (b - a) * (r - 1.0));
-        q = (qq - 1.0) * (r - 1.0) * (sq - 1.0);
+  auto solve = [&](double mu0, double slope_hint, double tol_f, int cap, int nf, const double *resum,
+                   int *used, Result *res) -> gf2_status {
+    gf2_status s;
+    int n = 0;
+    double last_mu = mu0, last_f = 0.0, prev_mu = 0.0, prev_f = 0.0;
+    bool have_prev = false;
+    auto eval = [&](double mu, double *f) -> gf2_status {
+      gf2_status e = count(mu, nf, resum, f);
+      if (e != GF2_OK) return e;
+      ++n;
+      if (n > 1) {
+        prev_mu = last_mu;
+        prev_f = last_f;
+        have_prev = true;
       }
-      if (p > 0.0) q = -q;
-      p = fabs(p);
-      if (2.0 * p < std::min(3.0 * xm * q - fabs(tol1 * q), fabs(e * q))) {
-        e = d;
-        d = p / q;
+      last_mu = mu;
+      last_f = *f;
+      return GF2_OK;
+    };
+    auto finish = [&](bool found) {
+      res->mu = last_mu;
+      res->found = found;
+      res->slope = (have_prev && last_mu != prev_mu) ? (last_f - prev_f) / (last_mu - prev_mu) : 0.0;
+      *used = n;
+      return GF2_OK;
+    };
+    double f0;
+    if ((s = eval(mu0, &f0)) != GF2_OK) return s;
+    if (fabs(f0) <= tol_f) return finish(true);
+    // N(mu) increases with mu; a slope hint sizes the first step to twice the Newton step
+    double step = (slope_hint > 0.0 && std::isfinite(slope_hint)) ? std::min(0.05, std::max(1e-12, 2.0 * fabs(f0) / slope_hint))
+                                                                    : 0.05;
+    double lo, hi, flo, fhi;
+    if (f0 < 0.0) {
+      lo = mu0; flo = f0; hi = mu0 + step;
+      for (;;) {
+        if (n >= cap) return finish(false);
+        if ((s = eval(hi, &fhi)) != GF2_OK) return s;
+        if (fabs(fhi) <= tol_f) return finish(true);
+        if (fhi > 0.0) break;
+        lo = hi; flo = fhi; step *= 2.0; hi += step;
+      }
+    } else {
+      hi = mu0; fhi = f0; lo = mu0 - step;
+      for (;;) {
+        if (n >= cap) return finish(false);
+        if ((s = eval(lo, &flo)) != GF2_OK) return s;
+        if (fabs(flo) <= tol_f) return finish(true);
+        if (flo < 0.0) break;
+        hi = lo; fhi = flo; step *= 2.0; lo -= step;
+      }
+    }
+    // Brent's method on the bracket: inverse quadratic interpolation or secant
+    // steps, falling back to bisection whenever they would not shrink it enough
+    double a = lo, fa = flo, b = hi, fb = fhi;
+    if (fabs(fa) < fabs(fb)) {
+      std::swap(a, b);
+      std::swap(fa, fb);
+    }
+    double c = a, fc = fa, d = b - a, e = d;
+    while (n < cap) {
+      if ((fb > 0.0) == (fc > 0.0)) {
+        c = a;
+        fc = fa;
+        d = e = b - a;
+      }
+      if (fabs(fc) < fabs(fb)) {
+        a = b; b = c; c = a;
+        fa = fb; fb = fc; fc = fa;
+      }
+      const double tol1 = 2.0 * 2.2e-16 * fabs(b) + 1e-16;
+      const double xm = 0.5 * (c - b);
+      if (fabs(xm) <= tol1) break;  // bracket collapsed without reaching tol
+      if (fabs(e) >= tol1 && fabs(fa) > fabs(fb)) {
+        const double sq = fb / fa;
+        double p, q;
+        if (a == c) {
+          p = 2.0 * xm * sq;
+          q = 1.0 - sq;
+        } else {
+          const double qq = fa / fc, r = fb / fc;
+          p = sq * (2.0 * xm * qq * (qq - r) - (b - a) * (r - 1.0));
+          q = (qq - 1.0) * (r - 1.0) * (sq - 1.0);
+        }
+        if (p > 0.0) q = -q;
+        p = fabs(p);
+        if (2.0 * p < std::min(3.0 * xm * q - fabs(tol1 * q), fabs(e * q))) {
+          e = d;
+          d = p / q;
+        } else {
+          d = xm;
+          e = d;
+        }
       } else {
         d = xm;
         e = d;
       }
-    } else {
-      d = xm;
-      e = d;
+      a = b;
+      fa = fb;
+      b += (fabs(d) > tol1) ? d : (xm > 0.0 ? tol1 : -tol1);
+      if ((s = eval(b, &fb)) != GF2_OK) return s;
+      if (fabs(fb) <= tol_f) return finish(true);
     }
-    a = b;
-    fa = fb;
-    b += (fabs(d) > tol1) ? d : (xm > 0.0 ? tol1 : -tol1);
-    if ((st = count(b, &fb)) != GF2_OK) return st;
-    last = b;
-    if (fabs(fb) <= tol) return done(b);
+    return finish(false);
+  };
+
+  // Coarse stage: the count over the lowest n_iw/8 frequencies (plus the
+  // analytic tail) differs from the full count by far less than the bracketing
+  // scale, so it locates mu and the local slope at an eighth of the cost.  The
+  // full-frequency stage then starts there with a slope-sized first step and
+  // decides convergence on the full count alone.
+  double mu_start = *mu_inout, slope = 0.0;
+  if (ctx->n_coarse > 0) {
+    Result rc;
+    int used = 0;
+    if ((st = solve(mu_start, 0.0, std::max(tol, 1e-9), 60, ctx->n_coarse, ctx->d_pole_resum + 4, &used, &rc)) !=
+        GF2_OK)
+      return st;
+    if (rc.found && std::isfinite(rc.mu)) {
+      mu_start = rc.mu;
+      slope = rc.slope;
+    }
   }
-  *mu_inout = last;
+  Result rf;
+  int used = 0;
+  st = solve(mu_start, slope, tol, max_iter, ctx->n_iw, ctx->d_pole_resum, &used, &rf);
   if (n_eval) *n_eval = evals;
-  return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: tolerance not reached");
+  if (st != GF2_OK) return st;
+  *mu_inout = rf.mu;
+  if (!rf.found) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: tolerance not reached");
+  return GF2_OK;
 }
 
 extern "C" gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_P, double *d_F) {

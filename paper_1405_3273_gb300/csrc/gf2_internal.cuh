@@ -54,7 +54,8 @@ struct gf2_ctx {
   double2 *d_twiddle = nullptr;   // e^{-2 pi i k / M}, k < M/2
   double2 *d_iw_pole = nullptr;   // [n_iw][4]: (i w_n - a)^-(r+1)
   double *d_tau_pole = nullptr;   // [n_tau][4]: tau image of (z - a)^-(r+1)
-  double *d_pole_resum = nullptr; // [4]: sum_{n<n_iw} Re (i w_n - a)^-(r+1)
+  double *d_pole_resum = nullptr; // [8]: sum_{n<n_iw}, then sum_{n<n_coarse}, of Re (i w_n - a)^-(r+1)
+  int n_coarse = 0;               // frequencies of a coarse particle count (0: none)
   double2 *d_t2w_w = nullptr;     // [n_iw]: h W(theta_n), attenuation factor
   double2 *d_t2w_corr = nullptr;  // [n_iw][8]: end corrections, nodes 0..3, M-3..M
 

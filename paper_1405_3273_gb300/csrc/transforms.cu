@@ -294,7 +294,7 @@ gf2_status gf2_tables_build(gf2_ctx *ctx) {
   GF2_CK(ctx, cudaMalloc(&ctx->d_twiddle, sizeof(double2) * (M / 2 + M)));
   GF2_CK(ctx, cudaMalloc(&ctx->d_iw_pole, sizeof(double2) * 4 * (size_t)n_iw));
   GF2_CK(ctx, cudaMalloc(&ctx->d_tau_pole, sizeof(double) * 4 * (size_t)n_tau));
-  GF2_CK(ctx, cudaMalloc(&ctx->d_pole_resum, sizeof(double) * 4));
+  GF2_CK(ctx, cudaMalloc(&ctx->d_pole_resum, sizeof(double) * 8));
   GF2_CK(ctx, cudaMalloc(&ctx->d_t2w_w, sizeof(double2) * (size_t)n_iw));
   GF2_CK(ctx, cudaMalloc(&ctx->d_t2w_corr, sizeof(double2) * 8 * (size_t)n_iw));
   const int total = std::max(std::max(M, n_tau), n_iw);
@@ -304,6 +304,12 @@ gf2_status gf2_tables_build(gf2_ctx *ctx) {
   GF2_CK_LAUNCH(ctx, "tables_kernel");
   pole_resum_kernel<<<1, 256, 0, ctx->stream>>>(n_iw, ctx->d_iw_pole, ctx->d_pole_resum);
   GF2_CK_LAUNCH(ctx, "pole_resum_kernel");
+  // the lowest n_iw / 8 frequencies serve the coarse counts of the mu search
+  ctx->n_coarse = (n_iw >= 2048) ? n_iw / 8 : 0;
+  if (ctx->n_coarse) {
+    pole_resum_kernel<<<1, 256, 0, ctx->stream>>>(ctx->n_coarse, ctx->d_iw_pole, ctx->d_pole_resum + 4);
+    GF2_CK_LAUNCH(ctx, "pole_resum_kernel");
+  }
   return GF2_OK;
 }
 

@@ -170,6 +170,31 @@ def test_mu_search_and_fock_match_oracle(library, h4):
     assert np.abs(got_F - oracle_fock(s.h, s.eri, P_ref)).max() < 1e-12
 
 
+def test_mu_search_coarse_stage_matches_oracle(library, h4):
+    """n_iw = 2048 switches on the coarse (n_iw/8 frequency) stage of the GPU
+    search; with a correlated Sigma the converged count and P must still match
+    the oracle's bisection on the full frequency sum."""
+    g = library
+    s, r = h4
+    beta, n_tau, n_iw = 50.0, 129, 2048
+    F, mu, G, P = og.inner_loop(s, r.F, None, None, None, beta, n_iw)
+    st = og.GF2State(F=F, mu=mu, P=P, G_iw=G, sig1=np.zeros_like(F), sig2=np.zeros_like(F))
+    _, Sig_tau = og.self_energy_step(s, st, beta, n_tau, n_iw)
+    Sig_iw = ot.tau_to_iw(Sig_tau, beta, n_iw)
+    sig1, sig2 = ot.sigma_expansion(Sig_tau, beta)
+    mu_ref, G_ref, P_ref, _ = od.mu_search(s.S, F, Sig_iw, sig1, sig2, s.n_elec, beta, n_iw)
+    with g.Context(s.nbf, n_tau, n_iw, beta) as ctx:
+        Gd = torch.zeros(n_iw, s.nbf, s.nbf, dtype=torch.complex128, device="cuda")
+        Pd = torch.zeros(s.nbf, s.nbf, dtype=torch.float64, device="cuda")
+        for start in (mu_ref + 0.05, mu_ref - 0.2):
+            got_mu, nev = g.gf2_mu_search(ctx.handle, dev(s.S), dev(F), dev(Sig_iw), dev(np.stack([sig1, sig2])),
+                                          s.n_elec, start, Gd, Pd)
+            Pn = host(Pd)
+            assert abs(np.trace(Pn @ s.S) - s.n_elec) <= 1e-10
+            assert np.abs(Pn - P_ref).max() < 1e-8
+            assert nev < 60
+
+
 def test_energy_matches_oracle(library, h4):
     g = library
     s, r = h4

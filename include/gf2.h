@@ -152,7 +152,7 @@ gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const double *d_momen
  * runs first: the same search on the count from the lowest n_iw/8 frequencies
  * plus the analytic tail (Dyson at an eighth of the cost), which places mu
  * and the local slope dN/dmu; the full-frequency search then starts there
- * with a first step of twice the Newton step.  Convergence is decided on the
+ * with the Newton step as its first probe.  Convergence is decided on the
  * full count only.  At most max_iter full evaluations (GF2_ERR_NOT_CONVERGED
  * beyond).  On success *mu_inout = mu, d_G_iw and d_P hold G(i w) and P at that
  * mu from a full evaluation, *n_eval (if not NULL) = number of Dyson

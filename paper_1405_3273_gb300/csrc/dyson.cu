@@ -482,8 +482,9 @@ extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const doubl
     double f0;
     if ((s = eval(mu0, &f0)) != GF2_OK) return s;
     if (fabs(f0) <= tol_f) return finish(true);
-    // N(mu) increases with mu; a slope hint sizes the first step to twice the Newton step
-    double step = (slope_hint > 0.0 && std::isfinite(slope_hint)) ? std::min(0.05, std::max(1e-12, 2.0 * fabs(f0) / slope_hint))
+    // N(mu) increases with mu; with a slope hint the first probe is the Newton
+    // step (it usually lands within tol; if it falls short the step doubles)
+    double step = (slope_hint > 0.0 && std::isfinite(slope_hint)) ? std::min(0.05, std::max(1e-12, fabs(f0) / slope_hint))
                                                                     : 0.05;
     double lo, hi, flo, fhi;
     if (f0 < 0.0) {

@@ -76,10 +76,36 @@ __device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
 }
 
 // write 64 consecutive fp32 values as one 256-byte row
+// (streaming stores: the row is read once, by the next kernel)
 __device__ __forceinline__ void store_row_f32(float *dst, const float *v) {
 #pragma unroll
   for (int c = 0; c < 16; ++c)
-    reinterpret_cast<float4 *>(dst)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    __stcs(reinterpret_cast<float4 *>(dst) + c, make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]));
+}
+
+// eight consecutive fp32 values -> T bf16 terms, 16 bytes per term at dst + t * plane
+template <int T>
+__device__ __forceinline__ void split8_store(const float *v, uint8_t *dst, uint32_t plane) {
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) x[e] = v[e];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    __nv_bfloat162 p[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) p[e] = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+    *reinterpret_cast<uint4 *>(dst + t * plane) =
+        make_uint4(*reinterpret_cast<const uint32_t *>(&p[0]), *reinterpret_cast<const uint32_t *>(&p[1]),
+                   *reinterpret_cast<const uint32_t *>(&p[2]), *reinterpret_cast<const uint32_t *>(&p[3]));
+    if (t + 1 < T) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(p[e]);
+        x[2 * e] -= f.x;
+        x[2 * e + 1] -= f.y;
+      }
+    }
+  }
 }
 
 // split four consecutive fp32 values into T bf16 terms; term t goes to the
@@ -228,6 +254,7 @@ __global__ void __launch_bounds__(320, 1)
   volatile int *abort = &s_abort;
 
   if (warp == 0 && lane == 0) {
+    const uint64_t stream_pol = tc::policy_evict_first();
     int it = 0, cur_c = -1, gcount = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
       const int c = u / (NP * 32), i = (u / 32) % NP, mt = u % 32;
@@ -243,7 +270,7 @@ __global__ void __launch_bounds__(320, 1)
       const int s = it % S;
       if (it >= S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::mbar_arrive_expect_tx(&full[s], kF32Tile);
-      tc::tma_load_3d(sA + s * A_STAGE + f32_offset<T>(), &map_t2, &full[s], mt * 128, 0, c * NP + i);
+      tc::tma_load_3d_hint(sA + s * A_STAGE + f32_offset<T>(), &map_t2, &full[s], mt * 128, 0, c * NP + i, stream_pol);
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0, gs = 0;
@@ -384,6 +411,7 @@ __global__ void __launch_bounds__(448, 1)
   const int npairs = n_units / NP;
 
   if (warp == 0 && lane == 0) {
+    const uint64_t stream_pol = tc::policy_evict_first(), keep_pol = tc::policy_evict_last();
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -394,9 +422,9 @@ __global__ void __launch_bounds__(448, 1)
         if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         uint8_t *st = smem + s * STAGE;
         tc::mbar_arrive_expect_tx(&full[s], kF32Tile + T * TILE64);
-        tc::tma_load_3d(st + f32_offset<T>(), &map_t3, &full[s], k0, cp * 128, 0);
+        tc::tma_load_3d_hint(st + f32_offset<T>(), &map_t3, &full[s], k0, cp * 128, 0, stream_pol);
         for (int t = 0; t < T; ++t)
-          tc::tma_load_3d(st + T * TILE128 + t * TILE64, &map_w, &full[s], k0, 0, t);
+          tc::tma_load_3d_hint(st + T * TILE128 + t * TILE64, &map_w, &full[s], k0, 0, t, keep_pol);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -550,10 +578,14 @@ __global__ void __launch_bounds__(320, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
+  // a contiguous block of units per CTA (balanced to within one unit)
+  const int u_begin = (int)((long long)blockIdx.x * n_units / gridDim.x);
+  const int u_end = (int)((long long)(blockIdx.x + 1) * n_units / gridDim.x);
 
   if (warp == 0 && lane == 0) {
+    const uint64_t keep_pol = tc::policy_evict_last();
     int it = 0, cur_cp = -1, gcount = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end; ++u, ++it) {
       const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
       if (cp != cur_cp) {
         const int gs = gcount % GS;
@@ -570,7 +602,7 @@ __global__ void __launch_bounds__(320, 1)
       if (it >= A1S && !tc::mbar_wait(&a1_empty[st], ((it / A1S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::mbar_arrive_expect_tx(&a1_full[st], A1_STAGE);
       for (int t = 0; t < T; ++t)
-        tc::tma_load_5d(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 2 * qp, 0, i, t);
+        tc::tma_load_5d_hint(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 2 * qp, 0, i, t, keep_pol);
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_cp = -1, gcount = 0, gs = 0;
@@ -598,7 +630,7 @@ __global__ void __launch_bounds__(320, 1)
       tc::mma_commit(&d2_full[db]);
       return true;
     };
-    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end && ok; ++u, ++it) {
       const int cp = u / (NP * 32);
       if (cp != cur_cp) {
         if (pend_u >= 0) {  // finish the previous pair before its G set can be recycled
@@ -651,7 +683,7 @@ __global__ void __launch_bounds__(320, 1)
     const int m = row >> 1, ql = row & 1;
     int it = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end && ok; ++u, ++it) {
       const int b = it & 1;
       if (!tc::mbar_wait(&d1_full[b], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
       tc::tc_fence_after();
@@ -671,21 +703,7 @@ __global__ void __launch_bounds__(320, 1)
         if (j >= A2S && !tc::mbar_wait(&a2_empty[ab], ((j / A2S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         uint8_t *dst = sA2 + ab * A2_BUF + ql * TILE64 + m * 128;
 #pragma unroll
-        for (int cch = 0; cch < 8; ++cch) {
-          __nv_bfloat16 p[8][T];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) tc::split_f32<T>(v[8 * cch + e], p[e]);
-          const int phys = cch ^ (m & 7);
-#pragma unroll
-          for (int t = 0; t < T; ++t) {
-            uint4 w;
-            w.x = tc::pack2(p[0][t], p[1][t]);
-            w.y = tc::pack2(p[2][t], p[3][t]);
-            w.z = tc::pack2(p[4][t], p[5][t]);
-            w.w = tc::pack2(p[6][t], p[7][t]);
-            *reinterpret_cast<uint4 *>(dst + t * TILE128 + phys * 16) = w;
-          }
-        }
+        for (int cch = 0; cch < 8; ++cch) split8_store<T>(v + 8 * cch, dst + ((cch ^ (m & 7)) << 4), TILE128);
         tc::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&a2_full[ab]);
@@ -697,7 +715,7 @@ __global__ void __launch_bounds__(320, 1)
     const int ql = row >> 6, l = row & 63;
     int j = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+    for (int u = u_begin; u < u_end && ok; ++u) {
       const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
       for (int s = 0; s < 2; ++s, ++j) {
         const int b = j & 1;

@@ -15,12 +15,15 @@ extern "C" {
 /* One 128 x 64 x 64 BF16 tile D = A B^T through TMA loads (128-byte swizzle),
  * four tcgen05.mma (K = 16 each, FP32 accumulation in TMEM) and tcgen05.ld.
  *   d_A: bf16, [128][64] row-major (M x K) if a_mn_major == 0,
- *        [64][128] row-major (K x M) if a_mn_major == 1;
+ *        [64][128] row-major (K x M) if a_mn_major == 1,
+ *        [128][64] row-major (M x K) written to TMEM by the threads and used as
+ *        the TMEM-resident A operand if a_mn_major == 2;
  *   d_B: bf16 [64][64] row-major (N x K);
  *   d_D: fp32 [128][64] row-major output;  d_err: device int, set non-zero
  *        if a pipeline wait timed out.
  * Device pointers owned by the caller; synchronizes `stream`.
- * GF2_ERR_ARG for NULL pointers, GF2_ERR_UNSUPPORTED without tensor maps. */
+ * GF2_ERR_ARG for NULL pointers or a_mn_major outside 0..2, GF2_ERR_UNSUPPORTED
+ * without tensor maps. */
 gf2_status gf2_test_umma_tile(int a_mn_major, const void *d_A, const void *d_B, float *d_D, int *d_err,
                               void *stream);
 

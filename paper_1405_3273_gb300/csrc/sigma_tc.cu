@@ -23,7 +23,10 @@
 // The intermediates T2 and T3 live in HBM as FP32 (4 bytes per value instead
 // of 2T for stored bf16 terms).  T bf16 terms of an FP32 value are formed by
 // the same rounding on either side of the store, so the operands the tensor
-// cores see are the same as if the terms had been stored.
+// cores see are the same as if the terms had been stored.  In xform and
+// contract the split A operand is written to TMEM by converter warps (one
+// thread per row, tcgen05.st) and read from there by tcgen05.mma, so shared
+// memory carries only the FP32 tiles and the B operand.
 //
 // All three are persistent, warp-specialised: one TMA producer thread, one
 // MMA-issuing thread, converter warps where an FP32 tile is split, and
@@ -108,36 +111,28 @@ __device__ __forceinline__ void split8_store(const float *v, uint8_t *dst, uint3
   }
 }
 
-// split four consecutive fp32 values into T bf16 terms; term t goes to the
-// 8 bytes at dst + t * plane (the operand planes of one tile).  Pairs are
-// rounded together (cvt.rn.bf16x2), so each term is the same round-to-nearest
-// split as tc::split_f32, and every residual is exact in fp32.
+// Split one row of 64 fp32 values (a TMEM lane of an A operand) into T bf16
+// terms and write term t as 32 packed columns at column taddr + 32 t.
 template <int T>
-__device__ __forceinline__ void split4_store(float4 x, uint8_t *dst, uint32_t plane) {
+__device__ __forceinline__ void split_row_to_tmem(float *x, uint32_t taddr) {
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
-    *reinterpret_cast<uint2 *>(dst + t * plane) =
-        make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
-    if (t + 1 < T) {
-      const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-      x.x -= fa.x;
-      x.y -= fa.y;
-      x.z -= fb.x;
-      x.w -= fb.y;
+    uint32_t w[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const __nv_bfloat162 p = __floats2bfloat162_rn(x[2 * c], x[2 * c + 1]);
+      w[c] = *reinterpret_cast<const uint32_t *>(&p);
+      if (t + 1 < T) {
+        const float2 f = __bfloat1622float2(p);
+        x[2 * c] -= f.x;
+        x[2 * c + 1] -= f.y;
+      }
     }
+    tc::tmem_st_32x32b_x32(taddr + 32 * t, w);
   }
 }
 
-// The converter warps of the xform and contract kernels turn an FP32 tile of
-// 128 x 64 values into T bf16 planes in place: the planes occupy the first
-// T * 16 KB of a stage and the TMA lands the FP32 tile in its last 32 KB.
-// Each of the four converter warps first reads its 16 rows of 16-byte chunks
-// into registers; after all four have read (a bounded mbarrier, so that a
-// timed-out pipeline cannot leave a warp waiting for ever) they write.
-constexpr uint32_t kF32Tile = 128 * NP * 4;  // 32 KB
-template <int T>
-__host__ __device__ constexpr uint32_t f32_offset() { return T * TILE128 - kF32Tile; }
+constexpr uint32_t kF32Tile = 128 * NP * 4;  // one FP32 tile of 128 x 64 values (32 KB)
 
 // ---------------------------------------------------------------------------
 // splitting of the FP64 inputs
@@ -207,34 +202,40 @@ __global__ void split_g_kernel(int N, int M, int k0, int count, int C, const dou
 // ---------------------------------------------------------------------------
 // stage 3: T3[c][i][l][n][p] = sum_q Gbar_c[p][q] T2[c][i][q][l][n]
 //
-// Unit (c, i, 128 rows of (l,n)).  The FP32 tile T2[c][i][q][(l,n)] arrives by
-// TMA; four converter warps split it in place into T bf16 planes laid out as
-// the MN-major, 128-byte-swizzled A operand; the MMA warp multiplies by the
-// Gbar planes; four epilogue warps store the FP32 rows T3[c][i][(l,n)][p].
+// Unit (c, i, 128 rows m of (l,n)).  The FP32 tile F[q][m] = T2[c][i][q][(l,n)]
+// arrives by TMA; each converter thread owns one row m (one TMEM lane), reads
+// its 64 values of q, splits them into T bf16 terms and writes them to TMEM as
+// the A operand (lane m, q packed two per column).  The MMA warp multiplies
+// A (TMEM) by the Gbar planes (shared memory); four epilogue warps store the
+// FP32 rows T3[c][i][(l,n)][p].  Keeping A in TMEM leaves shared memory to the
+// FP32 tiles and B, whose traffic otherwise bounds this kernel.
 // 320 threads: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue, warps 6-9 convert.
+// TMEM: accumulators at columns 0 and 64, A stages from column 128.
 // ---------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
                  float *__restrict__ t3, int C, int n_units, int *err) {
-  constexpr int S = (T == 2) ? 4 : 3;
-  constexpr uint32_t A_STAGE = T * TILE128, B_SET = T * TILE64;
+  constexpr int SF = 5, SA = 4;
+  constexpr uint32_t B_SET = T * TILE64, A_COLS = T * 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint8_t *sA = smem;
-  uint8_t *sB = sA + S * A_STAGE;
+  uint8_t *sF = smem;
+  uint8_t *sB = sF + SF * kF32Tile;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * B_SET);
-  uint64_t *full = bar, *rd = bar + S, *conv = bar + 2 * S, *empty = bar + 3 * S;
-  uint64_t *b_full = bar + 4 * S, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
+  uint64_t *f_full = bar, *f_empty = bar + SF, *a_full = bar + 2 * SF, *a_empty = a_full + SA;
+  uint64_t *b_full = a_empty + SA, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 8);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&rd[s], 4);
-      tc::mbar_init(&conv[s], 4);
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < SF; ++s) {
+      tc::mbar_init(&f_full[s], 1);
+      tc::mbar_init(&f_empty[s], 4);
+    }
+    for (int s = 0; s < SA; ++s) {
+      tc::mbar_init(&a_full[s], 4);
+      tc::mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&b_full[s], 1);
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(320, 1)
     tc::prefetch_tmap(&map_t2);
     tc::prefetch_tmap(&map_g);
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
@@ -267,10 +268,10 @@ __global__ void __launch_bounds__(320, 1)
         cur_c = c;
         ++gcount;
       }
-      const int s = it % S;
-      if (it >= S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
-      tc::mbar_arrive_expect_tx(&full[s], kF32Tile);
-      tc::tma_load_3d_hint(sA + s * A_STAGE + f32_offset<T>(), &map_t2, &full[s], mt * 128, 0, c * NP + i, stream_pol);
+      const int s = it % SF;
+      if (it >= SF && !tc::mbar_wait(&f_empty[s], ((it / SF) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::mbar_arrive_expect_tx(&f_full[s], kF32Tile);
+      tc::tma_load_3d_hint(sF + s * kF32Tile, &map_t2, &f_full[s], mt * 128, 0, c * NP + i, stream_pol);
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0, gs = 0;
@@ -283,20 +284,19 @@ __global__ void __launch_bounds__(320, 1)
         cur_c = c;
         ++gcount;
       }
-      const int s = it % S, d = it & 1;
-      if (!tc::mbar_wait(&conv[s], (it / S) & 1, abort)) { raise_abort(abort, err); break; }
+      const int sa = it % SA, d = it & 1;
+      if (!tc::mbar_wait(&a_full[sa], (it / SA) & 1, abort)) { raise_abort(abort, err); break; }
       if (it >= 2 && !tc::mbar_wait(&d_empty[d], ((it >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::tc_fence_after();
-      const uint32_t a0 = tc::smem_u32(sA + s * A_STAGE), b0 = tc::smem_u32(sB + gs * B_SET);
+      const uint32_t a0 = tmem + 128 + sa * A_COLS, b0 = tc::smem_u32(sB + gs * B_SET);
       for (int pr = 0; pr < Products<T>::n; ++pr) {
         const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = tc::smem_desc(a0 + ta * TILE128 + kk * 2048, TILE64, 1024);
           const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
-          tc::mma_bf16(tmem + d * 64, ad, bd, kIdescMK, (pr | kk) ? 1u : 0u);
+          tc::mma_bf16_ts(tmem + d * 64, a0 + ta * 32 + kk * 8, bd, kIdescKK, (pr | kk) ? 1u : 0u);
         }
       }
-      tc::mma_commit(&empty[s]);
+      tc::mma_commit(&a_empty[sa]);
       tc::mma_commit(&d_full[d]);
     }
   } else if (warp >= 2 && warp < 6) {
@@ -319,38 +319,34 @@ __global__ void __launch_bounds__(320, 1)
       store_row_f32(t3 + off, v);
     }
   } else if (warp >= 6) {
-    // converter: F[q][m] (fp32, m = 128 rows of (l,n)) -> A planes [h][q][64 m],
-    // 16-byte chunk (m % 64) / 8 stored at chunk ^ (q % 8).  Lane owns
-    // m = 4 lane .. +3; warp cw takes q = cw, cw + 4, ...
-    const int cw = warp - 6, h = lane >> 4, cc = (lane & 15) >> 1, half = lane & 1;
+    // converter: row m = 32 (warp % 4) + lane of the tile, the TMEM lane this warp may access
+    const int wq = warp & 3, m = wq * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + 128;
     int it = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
-      const int s = it % S;
-      const uint32_t par = (it / S) & 1;
-      if (!tc::mbar_wait(&full[s], par, abort)) { raise_abort(abort, err); break; }
-      uint8_t *stage = sA + s * A_STAGE;
-      float4 x[16];
+      const int s = it % SF, sa = it % SA;
+      if (!tc::mbar_wait(&f_full[s], (it / SF) & 1, abort)) { raise_abort(abort, err); break; }
+      float x[64];
+      const float *src = reinterpret_cast<const float *>(sF + s * kF32Tile) + m;
 #pragma unroll
-      for (int r = 0; r < 16; ++r)
-        x[r] = *reinterpret_cast<const float4 *>(stage + f32_offset<T>() + (4 * r + cw) * 512 + lane * 16);
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&rd[s]);
-      if (!tc::mbar_wait(&rd[s], par, abort)) { raise_abort(abort, err); break; }
-      uint8_t *dst = stage + h * TILE64 + half * 8;
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const int q = 4 * r + cw;
-        split4_store<T>(x[r], dst + q * 128 + ((cc ^ (q & 7)) << 4), TILE128);
-      }
+      for (int q = 0; q < 64; ++q) x[q] = src[q * 128];
+      // the next TMA write to this stage (async proxy) must follow these reads
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&conv[s]);
+      if (lane == 0) tc::mbar_arrive(&f_empty[s]);
+      if (it >= SA && !tc::mbar_wait(&a_empty[sa], ((it / SA) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      tc::tc_fence_after();
+      split_row_to_tmem<T>(x, lane_base + sa * A_COLS);
+      tc::tmem_st_wait();
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&a_full[sa]);
     }
   }
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 128);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -375,24 +371,32 @@ template <int T, int KSUB>
 __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
                     double *__restrict__ out, int N, int count, int C, int n_units, int *err) {
-  constexpr int S = (T == 2) ? 4 : 3;
+  constexpr int SF = 4, SW = 3, SA = 4;
   constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
   constexpr int NGROUP = KSTEPS / KSUB;
-  constexpr uint32_t STAGE = T * (TILE128 + TILE64);  // A planes (FP32 tile lands at the end), W planes
+  constexpr uint32_t W_STAGE = T * TILE64, A_COLS = T * 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S * STAGE);
-  uint64_t *full = bar, *rd = bar + S, *conv = bar + 2 * S, *empty = bar + 3 * S;
-  uint64_t *d_full = bar + 4 * S, *d_empty = d_full + 2;
+  uint8_t *sF = smem;                  // FP32 tiles [2 halves of 32 k][128 rows], 128-byte swizzle
+  uint8_t *sW = sF + SF * kF32Tile;    // W planes
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sW + SW * W_STAGE);
+  uint64_t *f_full = bar, *f_empty = bar + SF, *w_full = bar + 2 * SF, *w_empty = w_full + SW;
+  uint64_t *a_full = w_empty + SW, *a_empty = a_full + SA, *d_full = a_empty + SA, *d_empty = d_full + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_full + 4);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&rd[s], 4);
-      tc::mbar_init(&conv[s], 4);
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < SF; ++s) {
+      tc::mbar_init(&f_full[s], 1);
+      tc::mbar_init(&f_empty[s], 4);
+    }
+    for (int s = 0; s < SW; ++s) {
+      tc::mbar_init(&w_full[s], 1);
+      tc::mbar_init(&w_empty[s], 1);
+    }
+    for (int s = 0; s < SA; ++s) {
+      tc::mbar_init(&a_full[s], 4);
+      tc::mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(&d_full[s], 1);
@@ -403,10 +407,10 @@ __global__ void __launch_bounds__(448, 1)
     tc::prefetch_tmap(&map_t3);
     tc::prefetch_tmap(&map_w);
   }
-  if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  const uint32_t tmem = *tmem_slot;  // accumulators at columns 0 and 64, A stages from 128
   volatile int *abort = &s_abort;
   const int npairs = n_units / NP;
 
@@ -418,13 +422,16 @@ __global__ void __launch_bounds__(448, 1)
       const int l = u / npairs, cp = u % npairs;
       for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
         const int k0 = l * NP * NP + ks * NP;
-        const int s = g % S;
-        if (g >= S && !tc::mbar_wait(&empty[s], ((g / S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-        uint8_t *st = smem + s * STAGE;
-        tc::mbar_arrive_expect_tx(&full[s], kF32Tile + T * TILE64);
-        tc::tma_load_3d_hint(st + f32_offset<T>(), &map_t3, &full[s], k0, cp * 128, 0, stream_pol);
+        const int s = g % SF, sw = g % SW;
+        if (g >= SF && !tc::mbar_wait(&f_empty[s], ((g / SF) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::mbar_arrive_expect_tx(&f_full[s], kF32Tile);
+        for (int h = 0; h < 2; ++h)
+          tc::tma_load_3d_hint(sF + s * kF32Tile + h * (kF32Tile / 2), &map_t3, &f_full[s], k0 + 32 * h, cp * 128, 0,
+                               stream_pol);
+        if (g >= SW && !tc::mbar_wait(&w_empty[sw], ((g / SW) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::mbar_arrive_expect_tx(&w_full[sw], W_STAGE);
         for (int t = 0; t < T; ++t)
-          tc::tma_load_3d_hint(st + T * TILE128 + t * TILE64, &map_w, &full[s], k0, 0, t, keep_pol);
+          tc::tma_load_3d_hint(sW + sw * W_STAGE + t * TILE64, &map_w, &w_full[sw], k0, 0, t, keep_pol);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -436,19 +443,23 @@ __global__ void __launch_bounds__(448, 1)
         if (grp >= 2 && !tc::mbar_wait(&d_empty[d], ((grp >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
         for (int kq = 0; kq < KSUB; ++kq, ++g) {
-          const int s = g % S;
-          if (!tc::mbar_wait(&conv[s], (g / S) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+          const int sa = g % SA, sw = g % SW;
+          if (!tc::mbar_wait(&a_full[sa], (g / SA) & 1, abort) || !tc::mbar_wait(&w_full[sw], (g / SW) & 1, abort)) {
+            raise_abort(abort, err);
+            ok = false;
+            break;
+          }
           tc::tc_fence_after();
-          const uint32_t base = tc::smem_u32(smem + s * STAGE);
+          const uint32_t a0 = tmem + 128 + sa * A_COLS, b0 = tc::smem_u32(sW + sw * W_STAGE);
           for (int pr = 0; pr < Products<T>::n; ++pr) {
             const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ad = tc::smem_desc(base + ta * TILE128 + kk * 32, 16, 1024);
-              const uint64_t bd = tc::smem_desc(base + T * TILE128 + tb * TILE64 + kk * 32, 16, 1024);
-              tc::mma_bf16(tmem + d * 64, ad, bd, kIdescKK, (kq | pr | kk) ? 1u : 0u);
+              const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
+              tc::mma_bf16_ts(tmem + d * 64, a0 + ta * 32 + kk * 8, bd, kIdescKK, (kq | pr | kk) ? 1u : 0u);
             }
           }
-          tc::mma_commit(&empty[s]);
+          tc::mma_commit(&a_empty[sa]);
+          tc::mma_commit(&w_empty[sw]);
         }
         if (ok) tc::mma_commit(&d_full[d]);
       }
@@ -486,42 +497,47 @@ __global__ void __launch_bounds__(448, 1)
       }
     }
   } else if (warp >= 10) {
-    // converter: F[r][k] (fp32, 128 rows x 64 k) -> A planes [r][64 k], K-major,
-    // 16-byte chunk k / 8 stored at chunk ^ (r % 8).  A warp pass covers rows
-    // 2 rp, 2 rp + 1 (rp = cw, cw + 4, ...); lane owns k = 4 (lane % 16) .. +3
-    // of row 2 rp + lane / 16.
-    const int cw = warp - 10, rsub = lane >> 4, cc = (lane & 15) >> 1, half = lane & 1;
+    // converter: row r = 32 (warp % 4) + lane (the TMEM lane this warp may access).
+    // Half h of the FP32 tile holds k = 32 h .. +31 of all rows, 128 bytes a row,
+    // with 16-byte chunk c of row r stored at chunk c ^ (r % 8).
+    const int wq = warp & 3, r = wq * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + 128;
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
-        const int s = g % S;
-        const uint32_t par = (g / S) & 1;
-        if (!tc::mbar_wait(&full[s], par, abort)) { raise_abort(abort, err); ok = false; break; }
-        uint8_t *stage = smem + s * STAGE;
-        float4 x[16];
+        const int s = g % SF, sa = g % SA;
+        if (!tc::mbar_wait(&f_full[s], (g / SF) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        float x[64];
+        const uint8_t *row_base = sF + s * kF32Tile + r * 128;
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-          x[r] = *reinterpret_cast<const float4 *>(stage + f32_offset<T>() + (4 * r + cw) * 512 + lane * 16);
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&rd[s]);
-        if (!tc::mbar_wait(&rd[s], par, abort)) { raise_abort(abort, err); ok = false; break; }
-        uint8_t *dst = stage + half * 8;
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int row = 2 * (4 * r + cw) + rsub;
-          split4_store<T>(x[r], dst + row * 128 + ((cc ^ (row & 7)) << 4), TILE128);
-        }
+          for (int cch = 0; cch < 8; ++cch) {
+            const float4 q = *reinterpret_cast<const float4 *>(row_base + h * (kF32Tile / 2) + ((cch ^ (r & 7)) << 4));
+            x[32 * h + 4 * cch] = q.x;
+            x[32 * h + 4 * cch + 1] = q.y;
+            x[32 * h + 4 * cch + 2] = q.z;
+            x[32 * h + 4 * cch + 3] = q.w;
+          }
+        // the next TMA write to this stage (async proxy) must follow these reads
         tc::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&conv[s]);
+        if (lane == 0) tc::mbar_arrive(&f_empty[s]);
+        if (g >= SA && !tc::mbar_wait(&a_empty[sa], ((g / SA) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        tc::tc_fence_after();
+        split_row_to_tmem<T>(x, lane_base + sa * A_COLS);
+        tc::tmem_st_wait();
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&a_full[sa]);
       }
     }
   }
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, 128);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -810,6 +826,70 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// the same tile with A taken from TMEM: each thread writes its row of A
+// (64 bf16 = 32 packed columns) into TMEM, then one thread issues the MMAs
+__global__ void __launch_bounds__(128, 1)
+    umma_tile_ts_kernel(const __nv_bfloat16 *__restrict__ A, const __grid_constant__ CUtensorMap map_b,
+                        float *__restrict__ D, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *sB = smem;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + TILE64);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, row = warp * 32 + lane;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_barrier_init();
+    s_abort = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, 128);
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;  // D at columns 0..63, A at 64..95
+  volatile int *abort = &s_abort;
+  uint32_t w[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) w[c] = reinterpret_cast<const uint32_t *>(A + row * 64)[c];
+  tc::tmem_st_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + 64, w);
+  tc::tmem_st_wait();
+  tc::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::tc_fence_after();
+    tc::mbar_arrive_expect_tx(&bar[0], TILE64);
+    tc::tma_load_3d(sB, &map_b, &bar[0], 0, 0, 0);
+    if (tc::mbar_wait(&bar[0], 0, abort)) {
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(sB) + kk * 32, 16, 1024);
+        tc::mma_bf16_ts(tmem, tmem + 64 + kk * 8, bd, kIdescKK, kk ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[1]);
+    } else {
+      raise_abort(abort, err);
+    }
+  }
+  __syncwarp();
+  if (tc::mbar_wait(&bar[1], 0, abort)) {
+    tc::tc_fence_after();
+    float v[64];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    tc::tmem_ld_32x32b_x32(taddr, v);
+    tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+    tc::tmem_ld_wait();
+    for (int j = 0; j < 64; ++j) D[row * 64 + j] = v[j];
+  } else if (lane == 0) {
+    raise_abort(abort, err);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -829,14 +909,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // bf16 operand tiles use the 128-byte swizzle of the MMA layouts; fp32 tiles
 // (split on chip) are plain row-major
 bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-              const uint32_t *box, bool fp32 = false) {
+              const uint32_t *box, bool fp32 = false, bool fp32_swizzle = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   CUresult r = fn(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank,
                   const_cast<void *>(base), reinterpret_cast<const cuuint64_t *>(dims),
                   reinterpret_cast<const cuuint64_t *>(strides_bytes), reinterpret_cast<const cuuint32_t *>(box), es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, fp32 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  (fp32 && !fp32_swizzle) ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -856,9 +937,9 @@ size_t smem_sandwich() {
   return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
 }
 template <int T>
-size_t smem_xform() { return 1024 + ((T == 2) ? 4 : 3) * T * TILE128 + 2 * T * TILE64 + 256; }
+size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }
 template <int T>
-size_t smem_contract() { return 1024 + ((T == 2) ? 4 : 3) * T * (TILE128 + TILE64) + 256; }
+size_t smem_contract() { return 1024 + 4 * (size_t)kF32Tile + 3 * T * TILE64 + 256; }
 
 template <int T>
 gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int count, double *d_out) {
@@ -965,11 +1046,12 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     uint32_t box[3] = {128, 64, 1};
     ok &= make_map(&s->map_t2, s->T2, 3, dims, str, box, true);
   }
-  {  // T3 (fp32): dims (K = NP^3, rows (c,i) C*64, 1), box (64, 128, 1) -> F[row][64 k]
+  {  // T3 (fp32): dims (K = NP^3, rows (c,i) C*64, 1), box (32, 128, 1), 128-byte swizzle:
+     // F[row][32 k] per half of a 64-wide K step
     uint64_t dims[3] = {(uint64_t)NP * NP * NP, (uint64_t)C * NP, 1};
     uint64_t str[2] = {(uint64_t)NP * NP * NP * 4, (uint64_t)C * kPlane4 * 4};
-    uint32_t box[3] = {64, 128, 1};
-    ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box, true);
+    uint32_t box[3] = {32, 128, 1};
+    ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box, true, true);
   }
   {  // W: dims (K = NP^3, j 64, t), box (64, 64, 1)
     uint64_t dims[3] = {(uint64_t)NP * NP * NP, NP, TMAX};
@@ -1032,10 +1114,25 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, doub
 // test hook: one 128x64x64 BF16 tile through TMA, tcgen05.mma and tcgen05.ld
 extern "C" gf2_status gf2_test_umma_tile(int a_mn_major, const void *d_A, const void *d_B, float *d_D,
                                          int *d_err, void *stream) {
-  if (!d_A || !d_B || !d_D || !d_err) return GF2_ERR_ARG;
+  if (!d_A || !d_B || !d_D || !d_err || a_mn_major < 0 || a_mn_major > 2) return GF2_ERR_ARG;
   if (!encode_fn()) return GF2_ERR_UNSUPPORTED;
   CUtensorMap ma, mb;
   bool ok;
+  if (a_mn_major == 2) {  // A [M=128][K=64] bf16 through TMEM
+    uint64_t dims[3] = {64, 64, 1};
+    uint64_t str[2] = {64 * 2, 64 * 64 * 2};
+    uint32_t box[3] = {64, 64, 1};
+    if (!make_map(&mb, d_B, 3, dims, str, box)) return GF2_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t smem = 1024 + TILE64 + 256;
+    if (cudaFuncSetAttribute(umma_tile_ts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return GF2_ERR_CUDA;
+    umma_tile_ts_kernel<<<1, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16 *>(d_A), mb, d_D, d_err);
+    if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GF2_ERR_CUDA;
+    return GF2_OK;
+  }
   if (a_mn_major) {  // A stored [K=64][M=128]: dims (128, 64, 1), box (64, 64, 1)
     uint64_t dims[3] = {128, 64, 1};
     uint64_t str[2] = {128 * 2, 128 * 64 * 2};

@@ -42,13 +42,14 @@ def bf16_round(x):
     return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("mn_major", [0, 1])
+@pytest.mark.parametrize("mn_major", [0, 1, 2])
 def test_single_tile_operand_layouts(g, mn_major):
+    """K-major and MN-major A from shared memory, and A resident in TMEM (mode 2)."""
     rng = np.random.default_rng(42 + mn_major)
     A = bf16_round(rng.normal(size=(128, 64)))   # M x K
     B = bf16_round(rng.normal(size=(64, 64)))    # N x K
     ref = A.double() @ B.double().T
-    a_dev = (A.T.contiguous() if mn_major else A.contiguous()).cuda()
+    a_dev = (A.T.contiguous() if mn_major == 1 else A.contiguous()).cuda()
     b_dev = B.contiguous().cuda()
     D = torch.zeros(128, 64, dtype=torch.float32, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")

@@ -215,17 +215,19 @@ __global__ void split_g_kernel(int N, int M, int k0, int count, int C, const dou
 template <int T>
 __global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
-                 float *__restrict__ t3, int C, int n_units, int *err) {
-  constexpr int SF = 5, SA = 4;
+                 const __grid_constant__ CUtensorMap map_t3s, int C, int n_units, int *err) {
+  constexpr int SF = 4, SA = 4;
   constexpr uint32_t B_SET = T * TILE64, A_COLS = T * 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *sF = smem;
   uint8_t *sB = sF + SF * kF32Tile;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + 2 * B_SET);
+  uint8_t *sO = sB + 2 * B_SET;  // output tile [2 halves of 32 p][128 rows], 128-byte swizzle
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + kF32Tile);
   uint64_t *f_full = bar, *f_empty = bar + SF, *a_full = bar + 2 * SF, *a_empty = a_full + SA;
   uint64_t *b_full = a_empty + SA, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 8);
+  uint64_t *o_full = b_full + 8, *o_empty = b_full + 9;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 10);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -243,10 +245,13 @@ __global__ void __launch_bounds__(320, 1)
       tc::mbar_init(&d_full[s], 1);
       tc::mbar_init(&d_empty[s], 4);
     }
+    tc::mbar_init(o_full, 4);
+    tc::mbar_init(o_empty, 1);
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_t2);
     tc::prefetch_tmap(&map_g);
+    tc::prefetch_tmap(&map_t3s);
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
@@ -300,6 +305,8 @@ __global__ void __launch_bounds__(320, 1)
       tc::mma_commit(&d_full[d]);
     }
   } else if (warp >= 2 && warp < 6) {
+    // epilogue: D row -> the swizzled output tile (16-byte chunk j of row r of
+    // half h at chunk j ^ (r % 8)); warp 2 lane 0 stores the tile with TMA
     const int wq = warp & 3, row = wq * 32 + lane;
     int it = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
@@ -315,9 +322,30 @@ __global__ void __launch_bounds__(320, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&d_empty[d]);
-      const size_t off = (((size_t)c * NP + i) * (NP * NP) + (size_t)mt * 128 + row) * NP;
-      store_row_f32(t3 + off, v);
+      if (it >= 1 && !tc::mbar_wait(o_empty, (it - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      uint8_t *orow = sO + row * 128;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<float4 *>(orow + h * (kF32Tile / 2) + ((j ^ (row & 7)) << 4)) =
+              make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2], v[32 * h + 4 * j + 3]);
+      tc::fence_proxy_async_smem();  // these writes are read by the TMA store
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(o_full);
+      if (warp == 2) {  // the whole warp waits (uniform exit on a timeout); lane 0 issues
+        if (!tc::mbar_wait(o_full, it & 1, abort)) { raise_abort(abort, err); break; }
+        if (lane == 0) {
+          for (int h = 0; h < 2; ++h)
+            tc::tma_store_3d(&map_t3s, sO + h * (kF32Tile / 2), 32 * h, mt * 128, c * NP + i);
+          tc::tma_store_commit();
+          tc::tma_store_wait_read();
+          tc::mbar_arrive(o_empty);
+        }
+        __syncwarp();
+      }
     }
+    if (warp == 2 && lane == 0) tc::tma_store_wait_all();
   } else if (warp >= 6) {
     // converter: row m = 32 (warp % 4) + lane of the tile, the TMEM lane this warp may access
     const int wq = warp & 3, m = wq * 32 + lane;
@@ -926,7 +954,7 @@ struct TcState {
   int C = 0;
   __nv_bfloat16 *Gs = nullptr;
   float *T2 = nullptr, *T3 = nullptr;  // FP32 intermediates, C * NP^4 each
-  CUtensorMap map_v, map_g, map_t2, map_t3, map_w;
+  CUtensorMap map_v, map_g, map_t2, map_t3, map_t3s, map_w;
 };
 
 constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
@@ -937,7 +965,7 @@ size_t smem_sandwich() {
   return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
 }
 template <int T>
-size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }
+size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }  // 4 input tiles + 1 output tile
 template <int T>
 size_t smem_contract() { return 1024 + 4 * (size_t)kF32Tile + 3 * T * TILE64 + 256; }
 
@@ -961,7 +989,8 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
     GF2_PROF(ctx, GF2_K_XFORM,
-             (xform_kernel<T><<<std::min(u2, sms), 320, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->T3, C, u2, ctx->d_err)));
+             (xform_kernel<T><<<std::min(u2, sms), 320, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->map_t3s, C, u2,
+                                                                            ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "xform_kernel");
     const int u3 = (ce / 2) * NP;
     GF2_PROF(ctx, GF2_K_CONTRACT,
@@ -1052,6 +1081,13 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     uint64_t str[2] = {(uint64_t)NP * NP * NP * 4, (uint64_t)C * kPlane4 * 4};
     uint32_t box[3] = {32, 128, 1};
     ok &= make_map(&s->map_t3, s->T3, 3, dims, str, box, true, true);
+  }
+  {  // T3 (fp32) as stored by stage 3: dims (p 64, (l,n) 4096, (c,i) C*64), box (32, 128, 1),
+     // 128-byte swizzle: one half of the 64 p of 128 rows
+    uint64_t dims[3] = {NP, NP * NP, (uint64_t)C * NP};
+    uint64_t str[2] = {NP * 4, (uint64_t)NP * NP * NP * 4};
+    uint32_t box[3] = {32, 128, 1};
+    ok &= make_map(&s->map_t3s, s->T3, 3, dims, str, box, true, true);
   }
   {  // W: dims (K = NP^3, j 64, t), box (64, 64, 1)
     uint64_t dims[3] = {(uint64_t)NP * NP * NP, NP, TMAX};

@@ -6,8 +6,8 @@
 // Per chunk of C time points three kernels run back to back:
 //
 //  sandwich   stages 1+2 fused.  Unit (tau pair, i, q pair): the v tile
-//             V[(m,q), k] (128 x 64) is loaded once and used for both time
-//             points.  MMA1  D1[(m,q), l]   = sum_k V[(m,q),k] G[k,l]
+//             V[(q,m), k] (128 x 64) is loaded once and used for both time
+//             points.  MMA1  D1[(q,m), l]   = sum_k V[(q,m),k] G[k,l]
 //             (TMEM) -> split by four epilogue warps into an MN-major smem
 //             operand A2[(q,l), m] -> MMA2  D2[(q,l), n] = sum_m A2 G[m,n]
 //             -> four more warps store T2[tau][i][q][l][n] in FP32.
@@ -78,14 +78,6 @@ __device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
   atomicExch(err, kErrTimeout);
 }
 
-// write 64 consecutive fp32 values as one 256-byte row
-// (streaming stores: the row is read once, by the next kernel)
-__device__ __forceinline__ void store_row_f32(float *dst, const float *v) {
-#pragma unroll
-  for (int c = 0; c < 16; ++c)
-    __stcs(reinterpret_cast<float4 *>(dst) + c, make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]));
-}
-
 // eight consecutive fp32 values -> T bf16 terms, 16 bytes per term at dst + t * plane
 template <int T>
 __device__ __forceinline__ void split8_store(const float *v, uint8_t *dst, uint32_t plane) {
@@ -146,12 +138,12 @@ __device__ __forceinline__ void split_f64(double x, __nv_bfloat16 *p) {
   }
 }
 
-// Vs[t][i][m][q][k] = split_t v[i][m][q][k]  (zero outside N)
+// Vs[t][i][q][m][k] = split_t v[i][m][q][k]  (zero outside N)
 __global__ void split_v_kernel(int N, const double *__restrict__ v, __nv_bfloat16 *__restrict__ Vs) {
   const size_t plane = (size_t)NP * NP * NP * NP;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = idx % NP, q = (idx / NP) % NP, m = (idx / (NP * NP)) % NP, i = idx / (NP * NP * NP);
+    const int k = idx % NP, m = (idx / NP) % NP, q = (idx / (NP * NP)) % NP, i = idx / (NP * NP * NP);
     double x = 0.0;
     if (i < N && m < N && q < N && k < N)
       x = v[(((size_t)i * N + m) * N + q) * N + k];
@@ -574,14 +566,15 @@ __global__ void __launch_bounds__(448, 1)
 //
 // Unit = (tau pair, i, q pair).  MMA1 covers both time points at once: its B
 // operand stacks G(tau_a)^T and G(tau_b)^T (N = 128), so D1 holds
-// [(m,q), (s,l)] for s = 0, 1.  Each half becomes one job for epilogue 1
-// (D1 -> A2 smem, MN-major) and MMA2 (N = 64, one time point).
+// [(q,m), (s,l)] for s = 0, 1.  Each half becomes one job for epilogue 1
+// (D1 -> A2 smem, MN-major) and MMA2 (N = 64, one time point); epilogue 2
+// stores each D2 tile with TMA through a swizzled shared buffer.
 // TMEM: D1 buffers at columns 0 and 128 (128 wide), D2 buffers at 256, 320.
 // ---------------------------------------------------------------------------
 template <int T>
 __global__ void __launch_bounds__(320, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
-                    float *__restrict__ t2, int C, int n_units, int *err) {
+                    const __grid_constant__ CUtensorMap map_t2s, int C, int n_units, int *err) {
   constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
   constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
   constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
@@ -592,11 +585,12 @@ __global__ void __launch_bounds__(320, 1)
   uint8_t *sA1 = smem;
   uint8_t *sG = sA1 + A1S * A1_STAGE;  // per set: [t][s][64][64]
   uint8_t *sA2 = sG + GS * G_SET;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sA2 + A2S * A2_BUF);
+  uint8_t *sO = sA2 + A2S * A2_BUF;  // output tile [2 halves of 32 n][128 rows], 128-byte swizzle
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + kF32Tile);
   uint64_t *a1_full = bar, *a1_empty = bar + 2, *g_full = bar + 4, *g_empty = bar + 6;
   uint64_t *d1_full = bar + 8, *d1_empty = bar + 10, *a2_full = bar + 12, *a2_empty = bar + 14;
-  uint64_t *d2_full = bar + 16, *d2_empty = bar + 18;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 20);
+  uint64_t *d2_full = bar + 16, *d2_empty = bar + 18, *o_full = bar + 20, *o_empty = bar + 21;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 22);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -612,10 +606,13 @@ __global__ void __launch_bounds__(320, 1)
       tc::mbar_init(&d2_full[s], 1);
       tc::mbar_init(&d2_empty[s], 4);
     }
+    tc::mbar_init(o_full, 4);
+    tc::mbar_init(o_empty, 1);
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_v);
     tc::prefetch_tmap(&map_g);
+    tc::prefetch_tmap(&map_t2s);
   }
   if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
@@ -646,7 +643,7 @@ __global__ void __launch_bounds__(320, 1)
       if (it >= A1S && !tc::mbar_wait(&a1_empty[st], ((it / A1S) - 1) & 1, abort)) { raise_abort(abort, err); break; }
       tc::mbar_arrive_expect_tx(&a1_full[st], A1_STAGE);
       for (int t = 0; t < T; ++t)
-        tc::tma_load_5d_hint(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 2 * qp, 0, i, t, keep_pol);
+        tc::tma_load_5d_hint(sA1 + st * A1_STAGE + t * TILE128, &map_v, &a1_full[st], 0, 0, 2 * qp, i, t, keep_pol);
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_cp = -1, gcount = 0, gs = 0;
@@ -722,9 +719,10 @@ __global__ void __launch_bounds__(320, 1)
     if (ok && pend_u >= 0 && (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)))
       raise_abort(abort, err);
   } else if (warp >= 2 && warp < 6) {
-    // epilogue 1: D1[(m,q), (s,l)] -> A2_j[(q,l), m] (MN-major, 128-byte swizzle), j = 2 it + s
+    // epilogue 1: D1[(q,m), (s,l)] -> A2_j[(q,l), m] (MN-major, 128-byte swizzle), j = 2 it + s;
+    // a warp holds 32 consecutive m of one q, so its 16-byte stores hit distinct banks
     const int wq = warp & 3, row = wq * 32 + lane;
-    const int m = row >> 1, ql = row & 1;
+    const int m = row & 63, ql = row >> 6;
     int it = 0;
     bool ok = true;
     for (int u = u_begin; u < u_end && ok; ++u, ++it) {
@@ -756,7 +754,6 @@ __global__ void __launch_bounds__(320, 1)
   } else if (warp >= 6) {
     // epilogue 2: D2[(q,l), n] -> T2[c][i][q][l][n]
     const int wq = warp & 3, row = wq * 32 + lane;
-    const int ql = row >> 6, l = row & 63;
     int j = 0;
     bool ok = true;
     for (int u = u_begin; u < u_end && ok; ++u) {
@@ -773,11 +770,33 @@ __global__ void __launch_bounds__(320, 1)
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&d2_empty[b]);
-        const int c = 2 * cp + s, q = 2 * qp + ql;
-        const size_t off = ((((size_t)c * NP + i) * NP + q) * NP + l) * NP;
-        store_row_f32(t2 + off, v);
+        // row (ql, l) of the tile is row 128 qp + row of T2[c][i]; 16-byte chunk
+        // k of row r in half h sits at chunk k ^ (r % 8)
+        if (j >= 1 && !tc::mbar_wait(o_empty, (j - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        uint8_t *orow = sO + row * 128;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            *reinterpret_cast<float4 *>(orow + h * (kF32Tile / 2) + ((k ^ (row & 7)) << 4)) =
+                make_float4(v[32 * h + 4 * k], v[32 * h + 4 * k + 1], v[32 * h + 4 * k + 2], v[32 * h + 4 * k + 3]);
+        tc::fence_proxy_async_smem();  // these writes are read by the TMA store
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(o_full);
+        if (warp == 6) {  // the whole warp waits (uniform exit on a timeout); lane 0 issues
+          if (!tc::mbar_wait(o_full, j & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+          if (lane == 0) {
+            const int c = 2 * cp + s;
+            for (int h = 0; h < 2; ++h) tc::tma_store_3d(&map_t2s, sO + h * (kF32Tile / 2), 32 * h, qp * 128, c * NP + i);
+            tc::tma_store_commit();
+            tc::tma_store_wait_read();
+            tc::mbar_arrive(o_empty);
+          }
+          __syncwarp();
+        }
       }
     }
+    if (warp == 6 && lane == 0) tc::tma_store_wait_all();
   }
   __syncthreads();
   if (warp == 1) {
@@ -954,7 +973,7 @@ struct TcState {
   int C = 0;
   __nv_bfloat16 *Gs = nullptr;
   float *T2 = nullptr, *T3 = nullptr;  // FP32 intermediates, C * NP^4 each
-  CUtensorMap map_v, map_g, map_t2, map_t3, map_t3s, map_w;
+  CUtensorMap map_v, map_g, map_t2, map_t2s, map_t3, map_t3s, map_w;
 };
 
 constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
@@ -962,7 +981,7 @@ constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
 template <int T>
 size_t smem_sandwich() {
   const int GS = (T == 2) ? 2 : 1, A1S = (T == 2) ? 2 : 1, A2S = 2;
-  return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + 256;
+  return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + kF32Tile + 256;
 }
 template <int T>
 size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }  // 4 input tiles + 1 output tile
@@ -985,7 +1004,8 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     GF2_CK(ctx, cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cnt * N * N, ctx->stream));
     const int u1 = (ce / 2) * NP * 32;
     GF2_PROF(ctx, GF2_K_SANDWICH,
-             (sandwich_kernel<T><<<std::min(u1, sms), 320, ssw, ctx->stream>>>(s->map_v, s->map_g, s->T2, C, u1, ctx->d_err)));
+             (sandwich_kernel<T><<<std::min(u1, sms), 320, ssw, ctx->stream>>>(s->map_v, s->map_g, s->map_t2s, C, u1,
+                                                                                ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
     GF2_PROF(ctx, GF2_K_XFORM,
@@ -1057,10 +1077,10 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     return gf2_cuda_fail(ctx, e, "tc workspace");
   }
   bool ok = true;
-  {  // v: dims (k, q, m, i, t), box (64, 2, 64, 1, 1) -> rows (m, q) of 64 k
+  {  // v: dims (k, m, q, i, t), box (64, 64, 2, 1, 1) -> rows (q, m) of 64 k
     uint64_t dims[5] = {NP, NP, NP, NP, TMAX};
     uint64_t str[4] = {NP * 2, NP * NP * 2, (uint64_t)NP * NP * NP * 2, kPlane4 * 2};
-    uint32_t box[5] = {64, 2, 64, 1, 1};
+    uint32_t box[5] = {64, 64, 2, 1, 1};
     ok &= make_map(&s->map_v, ctx->d_v_split, 5, dims, str, box);
   }
   {  // G sets: dims (64, 64, 2*TMAX*C), box (64, 64, 1)
@@ -1074,6 +1094,13 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     uint64_t str[2] = {NP * NP * 4, (uint64_t)NP * NP * NP * 4};
     uint32_t box[3] = {128, 64, 1};
     ok &= make_map(&s->map_t2, s->T2, 3, dims, str, box, true);
+  }
+  {  // T2 (fp32) as stored by stages 1+2: dims (n 64, (q,l) 4096, (c,i) C*64), box (32, 128, 1),
+     // 128-byte swizzle: one half of the 64 n of 128 rows
+    uint64_t dims[3] = {NP, NP * NP, (uint64_t)C * NP};
+    uint64_t str[2] = {NP * 4, (uint64_t)NP * NP * NP * 4};
+    uint32_t box[3] = {32, 128, 1};
+    ok &= make_map(&s->map_t2s, s->T2, 3, dims, str, box, true, true);
   }
   {  // T3 (fp32): dims (K = NP^3, rows (c,i) C*64, 1), box (32, 128, 1), 128-byte swizzle:
      // F[row][32 k] per half of a 64-wide K step

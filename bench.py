@@ -317,13 +317,20 @@ def run_ours(args, rank, world, dist):
     else:
         achieved, peak = amount / dur / 1e9, hbm_gbs
     traffic = ncu_traffic(dom)
+    issued_factor = 6 if args.prec == "bf16x6" else 3
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if bound != "alu" else
                 "derived: 1.25 TFLOP/s FP64 nominal at 2070 MHz, scaled to the sampled clock"}
+    if bound == "tensor":
+        # split products actually issued on the tensor cores, and the DRAM rate of
+        # the kernel's measured traffic (its FP32 intermediates) against the copy peak
+        roofline["issued_frac"] = achieved * issued_factor / peak
+        if traffic:
+            roofline["traffic_gbs"] = traffic / dur / 1e9
+            roofline["traffic_frac_of_hbm"] = traffic / dur / 1e9 / hbm_gbs
     # the tensor kernels together
     tc_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sigma_sandwich", "sigma_xform", "sigma_contract")) / steps
-    issued_factor = 6 if args.prec == "bf16x6" else 3
 
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": steps,

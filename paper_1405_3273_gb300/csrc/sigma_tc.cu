@@ -374,10 +374,14 @@ __global__ void __launch_bounds__(320, 1)
 // stage 4: Sigma[c][i][j] -= sum_K T3[c][i][K] Ws[j][K],  split over K slices
 //
 // Each slice of NP*NP values of K is accumulated in groups of KSUB 64-wide
-// steps: the tensor cores sum one group in FP32 (TMEM, alternating between two
-// accumulators), and the epilogue adds every group into a compensated FP32
-// pair (TwoSum), so that the long sum never runs through a single FP32
-// accumulator.  The slice total enters the FP64 output through atomics.
+// steps: the tensor cores sum one group in FP32 (TMEM), and the epilogue adds
+// every group into a compensated FP32 pair (TwoSum), so that the long sum never
+// runs through a single FP32 accumulator.  The slice total enters the FP64
+// output through atomics.  The split products are issued as one MMA per A
+// term: A_a times the W planes 0 .. T-1-a stacked along N (N = 64 (T - a)), so
+// column block b of the accumulator collects A_a W_b for all a + b < T and the
+// epilogue adds the T blocks -- half the MMA instructions of one product per
+// instruction, with wider N.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   const float s = __fadd_rn(hi, x);
@@ -391,7 +395,8 @@ template <int T, int KSUB>
 __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
                     double *__restrict__ out, int N, int count, int C, int n_units, int *err) {
-  constexpr int SF = 4, SW = 3, SA = 4;
+  constexpr int SF = 4, SW = 3, SA = (T == 3) ? 3 : 4;
+  constexpr uint32_t D_COLS = T * 64;  // column block b accumulates sum_a A_a W_b
   constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
   constexpr int NGROUP = KSTEPS / KSUB;
   constexpr uint32_t W_STAGE = T * TILE64, A_COLS = T * 32;
@@ -401,8 +406,8 @@ __global__ void __launch_bounds__(448, 1)
   uint8_t *sW = sF + SF * kF32Tile;    // W planes
   uint64_t *bar = reinterpret_cast<uint64_t *>(sW + SW * W_STAGE);
   uint64_t *f_full = bar, *f_empty = bar + SF, *w_full = bar + 2 * SF, *w_empty = w_full + SW;
-  uint64_t *a_full = w_empty + SW, *a_empty = a_full + SA, *d_full = a_empty + SA, *d_empty = d_full + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_full + 4);
+  uint64_t *a_full = w_empty + SW, *a_empty = a_full + SA, *d_full = a_empty + SA, *d_empty = d_full + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_full + 2);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -418,10 +423,8 @@ __global__ void __launch_bounds__(448, 1)
       tc::mbar_init(&a_full[s], 4);
       tc::mbar_init(&a_empty[s], 1);
     }
-    for (int s = 0; s < 2; ++s) {
-      tc::mbar_init(&d_full[s], 1);
-      tc::mbar_init(&d_empty[s], 8);
-    }
+    tc::mbar_init(d_full, 1);
+    tc::mbar_init(d_empty, 8);
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_t3);
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(448, 1)
   if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;  // accumulators at columns 0 and 64, A stages from 128
+  const uint32_t tmem = *tmem_slot;  // accumulator at columns 0 .. D_COLS - 1, A stages after it
   volatile int *abort = &s_abort;
   const int npairs = n_units / NP;
 
@@ -459,8 +462,7 @@ __global__ void __launch_bounds__(448, 1)
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       for (int gi = 0; gi < NGROUP && ok; ++gi, ++grp) {
-        const int d = grp & 1;
-        if (grp >= 2 && !tc::mbar_wait(&d_empty[d], ((grp >> 1) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        if (grp >= 1 && !tc::mbar_wait(d_empty, (grp - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
         for (int kq = 0; kq < KSUB; ++kq, ++g) {
           const int sa = g % SA, sw = g % SW;
@@ -470,18 +472,20 @@ __global__ void __launch_bounds__(448, 1)
             break;
           }
           tc::tc_fence_after();
-          const uint32_t a0 = tmem + 128 + sa * A_COLS, b0 = tc::smem_u32(sW + sw * W_STAGE);
-          for (int pr = 0; pr < Products<T>::n; ++pr) {
-            const int ta = Products<T>::a(pr), tb = Products<T>::b(pr);
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t bd = tc::smem_desc(b0 + tb * TILE64 + kk * 32, 16, 1024);
-              tc::mma_bf16_ts(tmem + d * 64, a0 + ta * 32 + kk * 8, bd, kIdescKK, (kq | pr | kk) ? 1u : 0u);
-            }
+          const uint32_t a0 = tmem + D_COLS + sa * A_COLS, b0 = tc::smem_u32(sW + sw * W_STAGE);
+          // A_a times the W planes 0 .. T-1-a stacked along N: columns of plane b
+          // receive A_a W_b, so each block sums exactly the products a + b < T.
+          // The a = 0 product spans every column and opens the group.
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bd = tc::smem_desc(b0 + kk * 32, 16, 1024);
+            if (kq == 0 && kk == 0) tc::mma_bf16_ts(tmem, a0, bd, tc::idesc_bf16(128, T * 64, 0, 0), 0u);
+            for (int ta = T - 1; ta >= ((kq == 0 && kk == 0) ? 1 : 0); --ta)
+              tc::mma_bf16_ts(tmem, a0 + ta * 32 + kk * 8, bd, tc::idesc_bf16(128, (T - ta) * 64, 0, 0), 1u);
           }
           tc::mma_commit(&a_empty[sa]);
           tc::mma_commit(&w_empty[sw]);
         }
-        if (ok) tc::mma_commit(&d_full[d]);
+        if (ok) tc::mma_commit(d_full);
       }
     }
   } else if (warp >= 2 && warp < 10) {
@@ -495,17 +499,28 @@ __global__ void __launch_bounds__(448, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
       for (int gi = 0; gi < NGROUP; ++gi, ++grp) {
-        const int d = grp & 1;
-        if (!tc::mbar_wait(&d_full[d], (grp >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        if (!tc::mbar_wait(d_full, grp & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
-        float v[32];
-        tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(wq * 32) << 16) + d * 64 + col, v);
-        tc::tmem_ld_wait();
+        // sum the column blocks (smallest terms first), 16 columns at a time
+        const uint32_t dl = tmem + ((uint32_t)(wq * 32) << 16) + col;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          float v[16], w[16];
+          tc::tmem_ld_32x32b_x16(dl + 64 * (T - 1) + 16 * hh, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int bb = T - 2; bb >= 0; --bb) {
+            tc::tmem_ld_32x32b_x16(dl + 64 * bb + 16 * hh, w);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] += w[jj];
+          }
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) two_sum_acc(hi[16 * hh + jj], lo[16 * hh + jj], v[jj]);
+        }
         tc::tc_fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&d_empty[d]);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], v[j]);
+        if (lane == 0) tc::mbar_arrive(d_empty);
       }
       if (!ok) break;
       const int c = 2 * cp + row / NP, i = row % NP;
@@ -521,7 +536,7 @@ __global__ void __launch_bounds__(448, 1)
     // Half h of the FP32 tile holds k = 32 h .. +31 of all rows, 128 bytes a row,
     // with 16-byte chunk c of row r stored at chunk c ^ (r % 8).
     const int wq = warp & 3, r = wq * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + 128;
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + D_COLS;
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {

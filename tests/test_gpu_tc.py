@@ -105,6 +105,28 @@ def test_split_sigma_n64_sampled_points(g, prec, rtol):
         assert rel <= rtol, k
 
 
+@pytest.fixture(scope="module")
+def n64_every_point_case():
+    n, n_tau, count = 64, 65, 37
+    G = gi.random_symmetric_g(n, n_tau, seed=36)
+    v = gi.random_eri(n, seed=37)
+    return G, v, count, osg.sigma_tau(G, v, taus=range(count))
+
+
+@pytest.mark.parametrize("prec,rtol", [(2, 3e-6), (1, 5e-5)])
+def test_split_sigma_n64_every_point_full_chunk_and_ragged_tail(g, n64_every_point_case, prec, rtol):
+    """N = 64 with random symmetric G and v on a 65-point grid, the first 37 points
+    in one call: one full chunk of 32 and a last chunk of 5 (padded to three pairs),
+    every point against the oracle.  Each pipeline stage of the three kernels cycles
+    hundreds of times per CTA in the full chunk, so a stale or early-overwritten
+    buffer shows up as a bad point."""
+    G, v, count, ref = n64_every_point_case
+    got = _split_sigma(g, G, v, prec, count=count)
+    rel = np.abs(got - ref).max(axis=(1, 2)) / np.abs(ref).max()
+    print(f"split Sigma N=64 prec={prec}: worst point {int(rel.argmax())} at {rel.max():.2e}")
+    assert rel.max() <= rtol
+
+
 def test_split_sigma_points_offset_matches_full_grid(g):
     n, n_tau = 12, 17
     G = gi.random_symmetric_g(n, n_tau, seed=34)

@@ -16,7 +16,7 @@ step / step time (the Sigma-equivalent throughput of a whole iteration);
 the Sigma build alone, the FP64 GPU path (timed on sampled tau points and
 scaled) and a per-kernel breakdown are reported beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x6|bf16x3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x6|bf16x3|fp16x3|fp16x6]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
 """
 
@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = {"name": "h32_lattice_631g", "lattice": "2x4x4", "spacing_bohr": 2.0, "basis": "6-31g",
             "n_bf": 64, "n_elec": 32, "beta": 100.0, "n_tau": 4097, "n_iw": 8192}
 METRIC = "Σ(τ) s/iter & TFLOP/s at N=64: split-BF16 vs FP64 GPU path, |ΔE|≤1µEh"
-PRECS = {"bf16x3": 1, "bf16x6": 2, "fp64": 0}
+PRECS = {"bf16x3": 1, "bf16x6": 2, "fp16x3": 3, "fp16x6": 4, "fp64": 0}
+ISSUED = {"bf16x3": 3, "bf16x6": 6, "fp16x3": 3, "fp16x6": 6}   # split products per useful multiply
 
 
 def parse():
@@ -46,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x6", choices=sorted(ISSUED))
     ap.add_argument("--fp64-points", type=int, default=8, help="tau points for the FP64 path timing")
     ap.add_argument("--no-energy-check", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=4, help="tau points of the oracle CPU sample")
@@ -297,38 +298,58 @@ def run_ours(args, rank, world, dist):
     # dominant kernel and its roofline
     steps = args.steps
     per_kernel = {k: {"launches": c, "ms_per_step": ms / steps} for k, (c, ms) in prof.items()}
-    dom = max(prof, key=lambda k: prof[k][1])
-    n_launch, dom_ms = prof[dom]
-    dur = dom_ms / n_launch * 1e-3
+    issued_factor = ISSUED[args.prec]
     C = 32
-    work = {  # algorithmic work per launch
-        "sigma_sandwich": ("tensor", 4.0 * N ** 5 * C, "TFLOP/s"),
-        "sigma_xform": ("tensor", 2.0 * N ** 5 * C, "TFLOP/s"),
-        "sigma_contract": ("tensor", 2.0 * N ** 5 * C, "TFLOP/s"),
+    n4 = float(N) ** 4
+    # algorithmic work per launch (one chunk of C time points for the Sigma stages):
+    # useful flops of the stage, and the bytes of the stage's own input and output
+    # (T2 written by stages 1+2, T2 read and T3 written by stage 3, T3 read by
+    # stage 4, FP32).  A split contraction's peak is the BF16 peak divided by the
+    # split products issued per useful multiply.
+    tensor_work = {"sigma_sandwich": (4.0 * N ** 5 * C, 4.0 * n4 * C),
+                   "sigma_xform": (2.0 * N ** 5 * C, 8.0 * n4 * C),
+                   "sigma_contract": (2.0 * N ** 5 * C, 4.0 * n4 * C)}
+    other_work = {
         "dyson_inverse": ("alu", 8.0 * N ** 3 * n_iw, "TFLOP/s"),
         "fft_iw_to_tau": ("hbm", n_iw * N * N * 16 + n_tau * N * N * 8, "GB/s"),
         "fft_tau_to_iw": ("hbm", n_iw * N * N * 16 + n_tau * N * N * 8, "GB/s"),
     }
-    bound, amount, unit = work.get(dom, ("hbm", float("nan"), "GB/s"))
-    if bound == "tensor":
-        achieved, peak = amount / dur / 1e12, bf16_sust
-    elif bound == "alu":
-        achieved, peak = amount / dur / 1e12, 1.25 * (clocks["sm_mhz"] / 2070.0 if clocks else 1.0)
-    else:
-        achieved, peak = amount / dur / 1e9, hbm_gbs
-    traffic = ncu_traffic(dom)
-    issued_factor = 6 if args.prec == "bf16x6" else 3
-    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)" if bound != "alu" else
-                "derived: 1.25 TFLOP/s FP64 nominal at 2070 MHz, scaled to the sampled clock"}
-    if bound == "tensor":
-        # split products actually issued on the tensor cores, and the DRAM rate of
-        # the kernel's measured traffic (its FP32 intermediates) against the copy peak
-        roofline["issued_frac"] = achieved * issued_factor / peak
-        if traffic:
-            roofline["traffic_gbs"] = traffic / dur / 1e9
-            roofline["traffic_frac_of_hbm"] = traffic / dur / 1e9 / hbm_gbs
+    split_peak = bf16_sust / issued_factor
+
+    def roofline_of(k):
+        n_launch, k_ms = prof[k]
+        dur = k_ms / n_launch * 1e-3
+        if k in tensor_work:
+            flops, nbytes = tensor_work[k]
+            if nbytes / (hbm_gbs * 1e9) > flops / (split_peak * 1e12):
+                bound, achieved, peak, unit = "hbm", nbytes / dur / 1e9, hbm_gbs, "GB/s"
+                src = f"{peak_kind} HBM copy (MEASURED_PEAKS.json)"
+            else:
+                bound, achieved, peak, unit = "tensor", flops / dur / 1e12, split_peak, "TFLOP/s"
+                src = (f"{peak_kind} sustained BF16 {bf16_sust} TFLOP/s (MEASURED_PEAKS.json) / "
+                       f"{issued_factor} split products per useful flop")
+        else:
+            bound, amount, unit = other_work.get(k, ("hbm", float("nan"), "GB/s"))
+            if bound == "alu":
+                achieved, peak = amount / dur / 1e12, 1.25 * (clocks["sm_mhz"] / 2070.0 if clocks else 1.0)
+                src = "derived: 1.25 TFLOP/s FP64 nominal at 2070 MHz, scaled to the sampled clock"
+            else:
+                achieved, peak = amount / dur / 1e9, hbm_gbs
+                src = f"{peak_kind} HBM copy (MEASURED_PEAKS.json)"
+        traffic = ncu_traffic(k)
+        r = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+             "frac": achieved / peak, "traffic": traffic, "peak_source": src, "ms_per_launch": dur * 1e3}
+        if k in tensor_work:
+            r["useful_tflops"] = tensor_work[k][0] / dur / 1e12
+            r["issued_frac_of_bf16"] = tensor_work[k][0] * issued_factor / dur / 1e12 / bf16_sust
+            r["stage_io_gbs"] = tensor_work[k][1] / dur / 1e9
+            if traffic:
+                r["traffic_gbs"] = traffic / dur / 1e9
+        return r
+
+    dom = max(prof, key=lambda k: prof[k][1])
+    roofline = roofline_of(dom)
+    sigma_rooflines = {k: roofline_of(k) for k in tensor_work if k in prof}
     # the tensor kernels together
     tc_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("sigma_sandwich", "sigma_xform", "sigma_contract")) / steps
 
@@ -352,6 +373,7 @@ def run_ours(args, rank, world, dist):
         "mu_evaluations_per_step": log[-1][2],
         "kernels": per_kernel,
         "roofline": roofline,
+        "sigma_rooflines": sigma_rooflines,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": useful / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s",
@@ -434,7 +456,7 @@ def run_reference(args, rank, world, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, "
-                                f"n_tau={n_tau}, n_iw={n_iw}"),
+                                    f"n_tau={WORKLOAD['n_tau']}, n_iw={WORKLOAD['n_iw']}"),
                        "parallelism": "CPU oracle on the host cores"},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "each step: the oracle's rows timed on bounded samples (Sigma on a few tau "

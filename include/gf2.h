@@ -58,11 +58,20 @@ typedef enum {
  *                    three products hi*hi + hi*lo + lo*hi per multiply, FP32
  *                    accumulation on the tcgen05 tensor cores, FP64 for the
  *                    final sum over each block of the last contraction.
- *   GF2_PREC_BF16X6  three BF16 terms, six products (i + j <= 2). */
+ *   GF2_PREC_BF16X6  three BF16 terms, six products (i + j <= 2).
+ *   GF2_PREC_FP16X3  two FP16 terms, three products.  FP16 has three more
+ *                    significand bits than BF16 but a narrow exponent range, so
+ *                    v and W carry one power-of-two scale each, every G(tau)
+ *                    and G(-tau) its own (largest entry in [2^13, 2^14)), and
+ *                    each intermediate is scaled by 2^-20 before it is split;
+ *                    the scales are powers of two and are removed exactly.
+ *   GF2_PREC_FP16X6  three FP16 terms, six products, the same scaling. */
 typedef enum {
   GF2_PREC_FP64 = 0,
   GF2_PREC_BF16X3 = 1,
-  GF2_PREC_BF16X6 = 2
+  GF2_PREC_BF16X6 = 2,
+  GF2_PREC_FP16X3 = 3,
+  GF2_PREC_FP16X6 = 4
 } gf2_prec;
 
 typedef struct gf2_ctx gf2_ctx;
@@ -189,6 +198,42 @@ gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *d_F, const 
 gf2_status gf2_combine(gf2_ctx *ctx, int n, const double *coef, const double *const *d_src,
                        long long count, double *d_out);
 gf2_status gf2_gram(gf2_ctx *ctx, int n, const double *const *d_vecs, long long count, double *gram_out);
+
+/* ---- Batched Eq. Sigma over many systems of uneven size ----
+ * The paper builds Sigma(tau) one system at a time; the batch runs the Sigma
+ * builds of many independent systems (molecules, geometries) together on one
+ * GPU.  Instance i has n_bf[i] basis functions (1..112) and n_tau[i] time
+ * points (the gf2_create rules).  Every instance owns a context; the batch
+ * also creates up to four worker streams that fork from and join back into
+ * `stream` (a cudaStream_t, NULL = legacy default stream).
+ *   gf2_batch_set_system: integrals v [N^4] of an instance (copied) and its
+ *     overlap S [N][N] (may be NULL: no orthogonalisation, as gf2_set_overlap).
+ *   gf2_batch_tune: autotuner.  For every instance it times each admissible
+ *     path on one chunk of 32 points of d_G_tau[i] -- the FP64 staged
+ *     contraction, and for N <= 64 the split tensor-core pipeline in `prec` --
+ *     keeps the fastest (FP64 is always admissible, being more accurate), and
+ *     spreads the instances over the worker streams, longest estimated time
+ *     first.  d_G_tau: host array of n_inst device pointers [n_tau[i]][N][N].
+ *   gf2_batch_plan: the tuner's choice for one instance: precision code it
+ *     runs with, estimated ms of one full-grid build, worker stream index.
+ *   gf2_sigma_tau_batched: d_Sigma_tau[i] [n_tau[i]][N][N] <- Eq. Sigma of
+ *     instance i from d_G_tau[i] (host arrays of device pointers).  Tunes first
+ *     if `prec` differs from the last tuning.  The first call with a given set
+ *     of buffers records every instance's launches into one CUDA graph; later
+ *     calls with the same buffers (contents may change) replay it with one
+ *     graph launch.  Synchronizes `stream`, then checks every instance's
+ *     pipeline error word (GF2_ERR_TIMEOUT if a wait gave up).
+ *   Errors: GF2_ERR_ARG for bad sizes, instances or NULL pointers; instance
+ *   failures are reported with the instance index by gf2_batch_last_error. */
+typedef struct gf2_batch gf2_batch;
+gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n_bf, const int *n_tau, void *stream);
+gf2_status gf2_batch_destroy(gf2_batch *b);
+const char *gf2_batch_last_error(const gf2_batch *b);
+gf2_status gf2_batch_set_system(gf2_batch *b, int inst, const double *d_v, const double *d_S);
+gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau, int prec);
+gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane);
+gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, double *const *d_Sigma_tau,
+                                 int prec);
 
 /* Allocation-free Galitskii-Migdal energy (no counterpart in the paper).
  * Same inputs, outputs and arithmetic as gf2_energy, but without a context

@@ -21,6 +21,8 @@ GF2_OK = 0
 GF2_PREC_FP64 = 0
 GF2_PREC_BF16X3 = 1
 GF2_PREC_BF16X6 = 2
+GF2_PREC_FP16X3 = 3
+GF2_PREC_FP16X6 = 4
 STATUS_NAMES = {0: "GF2_OK", 1: "GF2_ERR_ARG", 2: "GF2_ERR_CUDA", 3: "GF2_ERR_NOMEM",
                 4: "GF2_ERR_NOT_CONVERGED", 5: "GF2_ERR_TIMEOUT", 6: "GF2_ERR_NONFINITE",
                 7: "GF2_ERR_UNSUPPORTED"}
@@ -51,6 +53,13 @@ _SIGS = {
     "gf2_combine": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.c_longlong, _P],
     "gf2_gram": [_P, _I, ctypes.POINTER(_P), ctypes.c_longlong, ctypes.POINTER(_D)],
     "gf2_energy_noalloc": [_I, _I, _D, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
+    "gf2_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
+    "gf2_batch_destroy": [_P],
+    "gf2_batch_last_error": [_P],
+    "gf2_batch_set_system": [_P, _I, _P, _P],
+    "gf2_batch_tune": [_P, ctypes.POINTER(_P), _I],
+    "gf2_batch_plan": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)],
+    "gf2_sigma_tau_batched": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I],
     "gf2_profile": [_P, _I],
     "gf2_profile_report": [_P, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -72,7 +81,8 @@ def lib():
         for name, args in _SIGS.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name in ("gf2_status_string", "gf2_last_error") else _I
+            f.restype = ctypes.c_char_p if name in ("gf2_status_string", "gf2_last_error",
+                                                    "gf2_batch_last_error") else _I
         _lib = L
     return _lib
 
@@ -223,6 +233,77 @@ def gf2_profile_report(ctx):
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out, n.value
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[_ptr(t, _F64).value for t in ts])
+
+
+def _check_batch(status, b):
+    if status != GF2_OK:
+        raise GF2Error(status, lib().gf2_batch_last_error(b).decode() if b else "")
+
+
+def gf2_batch_last_error(b):
+    return lib().gf2_batch_last_error(b).decode()
+
+
+def gf2_batch_create(n_bf, n_tau):
+    n = len(n_bf)
+    h = ctypes.c_void_p()
+    st = lib().gf2_batch_create(ctypes.byref(h), n, (ctypes.c_int * n)(*map(int, n_bf)),
+                                (ctypes.c_int * n)(*map(int, n_tau)), _stream())
+    if st != GF2_OK:
+        raise GF2Error(st, "gf2_batch_create rejected the sizes or could not allocate")
+    return h
+
+
+def gf2_batch_destroy(b):
+    _check(lib().gf2_batch_destroy(b), None)
+
+
+def gf2_batch_set_system(b, inst, v, S=None):
+    _check_batch(lib().gf2_batch_set_system(b, int(inst), _ptr(v, _F64), _ptr(S, _F64)), b)
+
+
+def gf2_batch_tune(b, G_taus, prec):
+    _check_batch(lib().gf2_batch_tune(b, _ptr_array(G_taus), int(prec)), b)
+
+
+def gf2_batch_plan(b, inst):
+    """(precision code, estimated ms per full-grid build, worker stream) chosen for an instance."""
+    p, ms, lane = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    _check_batch(lib().gf2_batch_plan(b, int(inst), ctypes.byref(p), ctypes.byref(ms), ctypes.byref(lane)), b)
+    return p.value, ms.value, lane.value
+
+
+def gf2_sigma_tau_batched(b, G_taus, Sigma_taus, prec):
+    _check_batch(lib().gf2_sigma_tau_batched(b, _ptr_array(G_taus), _ptr_array(Sigma_taus), int(prec)), b)
+
+
+class Batch:
+    """Owning handle around a gf2_batch (destroyed on close / garbage collection)."""
+
+    def __init__(self, n_bf, n_tau):
+        self.n_bf, self.n_tau = list(n_bf), list(n_tau)
+        self.handle = gf2_batch_create(self.n_bf, self.n_tau)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gf2_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Context:

@@ -1,0 +1,289 @@
+// Eq. Sigma for a batch of independent systems of uneven size on one GPU.
+//
+// Each instance keeps its own context (integrals, split planes, workspace).
+// An autotuner times the candidate paths of every instance on one chunk of
+// its own time grid -- the FP64 staged contraction on the CUDA cores, and the
+// split tensor-core pipeline (padded to 64 basis functions) when N <= 64 --
+// and keeps the fastest; the FP64 path is always admissible, being the more
+// accurate.  Instances are then spread over a few worker streams by longest
+// estimated time first, and the whole batched build is recorded once into a
+// CUDA graph: a fork from the caller's stream, every instance's launches on its
+// lane, a join back.  Later calls with the same buffers replay the graph with
+// one launch; the error words of the split kernels are read once afterwards.
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gf2_internal.cuh"
+
+struct gf2_batch {
+  int n = 0;
+  std::vector<gf2_ctx *> ctx;
+  std::vector<int> N, n_tau;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+  // autotuner result
+  int tuned_prec = -1;
+  std::vector<int> path;       // precision code each instance runs with
+  std::vector<double> est_ms;  // estimated ms of one full-grid Sigma build
+  std::vector<int> lane_of;
+  // recorded graph and the buffers it was recorded with
+  cudaGraphExec_t exec = nullptr;
+  int graph_prec = -1;
+  std::vector<const double *> graph_g;
+  std::vector<double *> graph_s;
+  std::string last_error;
+};
+
+namespace {
+
+constexpr int kMaxLanes = 4;
+constexpr int kTcMaxN = 64;
+
+gf2_status bfail(gf2_batch *b, gf2_status s, const std::string &m) {
+  if (b) b->last_error = m;
+  return s;
+}
+
+gf2_status from_ctx(gf2_batch *b, int i, gf2_status s) {
+  if (s != GF2_OK) b->last_error = "instance " + std::to_string(i) + ": " + gf2_last_error(b->ctx[i]);
+  return s;
+}
+
+bool split_prec(int p) {
+  return p == GF2_PREC_BF16X3 || p == GF2_PREC_BF16X6 || p == GF2_PREC_FP16X3 || p == GF2_PREC_FP16X6;
+}
+
+void drop_graph(gf2_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_prec = -1;
+  b->graph_g.clear();
+  b->graph_s.clear();
+}
+
+void release(gf2_batch *b) {
+  drop_graph(b);
+  for (auto c : b->ctx)
+    if (c) gf2_destroy(c);
+  for (auto s : b->lanes) cudaStreamDestroy(s);
+  for (auto e : b->ev_join) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+}
+
+// time one call of `prec` on instance i over `count` points from k0 (second of two calls)
+gf2_status time_path(gf2_batch *b, int i, const double *d_G, double *d_out, int k0, int count, int prec,
+                     double *ms) {
+  gf2_ctx *c = b->ctx[i];
+  gf2_set_stream(c, b->origin);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return bfail(b, GF2_ERR_CUDA, "autotuner: cudaEventCreate");
+  gf2_status st = gf2_sigma_tau_points(c, d_G, k0, count, d_out, prec);  // also allocates the workspace
+  if (st == GF2_OK) {
+    cudaEventRecord(e0, b->origin);
+    st = gf2_sigma_tau_points(c, d_G, k0, count, d_out, prec);
+    cudaEventRecord(e1, b->origin);
+  }
+  float t = 0.f;
+  if (st == GF2_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+    st = bfail(b, GF2_ERR_CUDA, "autotuner: event timing");
+  else if (st != GF2_OK)
+    from_ctx(b, i, st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t;
+  return st;
+}
+
+}  // namespace
+
+extern "C" gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n_bf, const int *n_tau, void *stream) {
+  if (!out) return GF2_ERR_ARG;
+  *out = nullptr;
+  if (n_inst < 1 || n_inst > 4096 || !n_bf || !n_tau) return GF2_ERR_ARG;
+  gf2_batch *b = new (std::nothrow) gf2_batch();
+  if (!b) return GF2_ERR_NOMEM;
+  b->n = n_inst;
+  b->origin = reinterpret_cast<cudaStream_t>(stream);
+  b->ctx.assign(n_inst, nullptr);
+  b->N.assign(n_bf, n_bf + n_inst);
+  b->n_tau.assign(n_tau, n_tau + n_inst);
+  gf2_status st = GF2_OK;
+  for (int i = 0; i < n_inst && st == GF2_OK; ++i)
+    st = gf2_create(&b->ctx[i], n_bf[i], n_tau[i], 8, 1.0, stream);  // Sigma(tau) uses no frequency grid
+  const int L = std::min(kMaxLanes, n_inst);
+  for (int l = 0; l < L && st == GF2_OK; ++l) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = GF2_ERR_CUDA;
+    else b->lanes.push_back(s);
+    if (st == GF2_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = GF2_ERR_CUDA;
+    else if (st == GF2_OK) b->ev_join.push_back(e);
+  }
+  if (st == GF2_OK && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) st = GF2_ERR_CUDA;
+  if (st != GF2_OK) {
+    release(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_batch_destroy(gf2_batch *b) {
+  if (!b) return GF2_ERR_ARG;
+  cudaStreamSynchronize(b->origin);
+  release(b);
+  delete b;
+  return GF2_OK;
+}
+
+extern "C" const char *gf2_batch_last_error(const gf2_batch *b) { return b ? b->last_error.c_str() : ""; }
+
+extern "C" gf2_status gf2_batch_set_system(gf2_batch *b, int inst, const double *d_v, const double *d_S) {
+  if (!b) return GF2_ERR_ARG;
+  if (inst < 0 || inst >= b->n || !d_v) return bfail(b, GF2_ERR_ARG, "gf2_batch_set_system: bad instance or NULL v");
+  drop_graph(b);
+  b->tuned_prec = -1;
+  gf2_ctx *c = b->ctx[inst];
+  gf2_set_stream(c, b->origin);
+  gf2_status st = gf2_set_integrals(c, d_v);
+  if (st == GF2_OK && d_S) st = gf2_set_overlap(c, d_S);
+  return from_ctx(b, inst, st);
+}
+
+extern "C" gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau, int prec) {
+  if (!b) return GF2_ERR_ARG;
+  if (!d_G_tau) return bfail(b, GF2_ERR_ARG, "gf2_batch_tune: NULL pointer array");
+  if (prec != GF2_PREC_FP64 && !split_prec(prec)) return bfail(b, GF2_ERR_ARG, "gf2_batch_tune: unknown precision");
+  for (int i = 0; i < b->n; ++i) {
+    if (!d_G_tau[i]) return bfail(b, GF2_ERR_ARG, "gf2_batch_tune: NULL G(tau) of an instance");
+    if (!b->ctx[i]->have_integrals) return bfail(b, GF2_ERR_ARG, "gf2_batch_tune: gf2_batch_set_system not called");
+  }
+  drop_graph(b);
+  b->path.assign(b->n, GF2_PREC_FP64);
+  b->est_ms.assign(b->n, 0.0);
+  b->lane_of.assign(b->n, 0);
+  // one chunk of the split pipeline (32 points) is the sample for every candidate
+  size_t out_elems = 0;
+  for (int i = 0; i < b->n; ++i) out_elems = std::max(out_elems, (size_t)32 * b->N[i] * b->N[i]);
+  double *d_out = nullptr;
+  if (cudaMalloc(&d_out, out_elems * sizeof(double)) != cudaSuccess)
+    return bfail(b, GF2_ERR_NOMEM, "gf2_batch_tune: sample buffer");
+  gf2_status st = GF2_OK;
+  for (int i = 0; i < b->n && st == GF2_OK; ++i) {
+    const int count = std::min(32, b->n_tau[i]);
+    std::vector<int> cands{GF2_PREC_FP64};
+    if (split_prec(prec) && b->N[i] <= kTcMaxN) cands.push_back(prec);
+    double best = 0.0;
+    for (int p : cands) {
+      double ms = 0.0;
+      if ((st = time_path(b, i, d_G_tau[i], d_out, 0, count, p, &ms)) != GF2_OK) break;
+      const double full = ms * b->n_tau[i] / count;
+      if (p == cands.front() || full < best) {
+        best = full;
+        b->path[i] = p;
+      }
+    }
+    b->est_ms[i] = best;
+    // keep only the workspace of the chosen path (a split chunk holds 4.3 GB of intermediates)
+    gf2_ctx *c = b->ctx[i];
+    if (cudaStreamSynchronize(b->origin) != cudaSuccess) st = bfail(b, GF2_ERR_CUDA, "autotuner: sync");
+    if (b->path[i] == GF2_PREC_FP64) {
+      gf2_tc_release(c);
+    } else if (c->d_ws) {
+      cudaFree(c->d_ws);
+      c->d_ws = nullptr;
+      c->ws_elems = 0;
+    }
+  }
+  cudaFree(d_out);
+  if (st != GF2_OK) return st;
+  // longest estimated time first, each to the least-loaded lane
+  std::vector<int> order(b->n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->est_ms[x] > b->est_ms[y]; });
+  std::vector<double> load(b->lanes.size(), 0.0);
+  for (int i : order) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->lane_of[i] = l;
+    load[l] += b->est_ms[i];
+  }
+  b->tuned_prec = prec;
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane) {
+  if (!b || inst < 0 || inst >= b->n || b->tuned_prec < 0) return GF2_ERR_ARG;
+  if (path) *path = b->path[inst];
+  if (est_ms) *est_ms = b->est_ms[inst];
+  if (lane) *lane = b->lane_of[inst];
+  return GF2_OK;
+}
+
+extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, double *const *d_Sigma_tau,
+                                            int prec) {
+  if (!b) return GF2_ERR_ARG;
+  if (!d_G_tau || !d_Sigma_tau) return bfail(b, GF2_ERR_ARG, "gf2_sigma_tau_batched: NULL pointer array");
+  for (int i = 0; i < b->n; ++i)
+    if (!d_G_tau[i] || !d_Sigma_tau[i]) return bfail(b, GF2_ERR_ARG, "gf2_sigma_tau_batched: NULL buffer");
+  gf2_status st;
+  if (b->tuned_prec != prec && (st = gf2_batch_tune(b, d_G_tau, prec)) != GF2_OK) return st;
+  const bool same = b->exec && b->graph_prec == prec &&
+                    std::equal(b->graph_g.begin(), b->graph_g.end(), d_G_tau) &&
+                    std::equal(b->graph_s.begin(), b->graph_s.end(), d_Sigma_tau);
+  if (!same) {
+    drop_graph(b);
+    // relaxed: the recorded calls set kernel attributes, which the stricter modes refuse
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    st = e == cudaSuccess ? GF2_OK : bfail(b, GF2_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    if (st == GF2_OK) cudaEventRecord(b->ev_fork, b->origin);
+    for (size_t l = 0; l < b->lanes.size() && st == GF2_OK; ++l) {
+      cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0);
+      for (int i = 0; i < b->n && st == GF2_OK; ++i) {
+        if (b->lane_of[i] != (int)l) continue;
+        gf2_ctx *c = b->ctx[i];
+        gf2_set_stream(c, b->lanes[l]);
+        c->defer_error_check = true;
+        st = from_ctx(b, i, gf2_sigma_tau(c, d_G_tau[i], d_Sigma_tau[i], b->path[i]));
+        c->defer_error_check = false;
+      }
+      cudaEventRecord(b->ev_join[l], b->lanes[l]);
+      cudaStreamWaitEvent(b->origin, b->ev_join[l], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->origin, &graph);
+    if (st == GF2_OK && e != cudaSuccess)
+      st = bfail(b, GF2_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    if (st == GF2_OK) {
+      e = cudaGraphInstantiate(&b->exec, graph, 0);
+      if (e != cudaSuccess) {
+        b->exec = nullptr;
+        st = bfail(b, GF2_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < b->n; ++i) gf2_set_stream(b->ctx[i], b->origin);
+    if (st != GF2_OK) return st;
+    b->graph_prec = prec;
+    b->graph_g.assign(d_G_tau, d_G_tau + b->n);
+    b->graph_s.assign(d_Sigma_tau, d_Sigma_tau + b->n);
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, b->origin);
+  if (e != cudaSuccess) return bfail(b, GF2_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  if ((e = cudaStreamSynchronize(b->origin)) != cudaSuccess)
+    return bfail(b, GF2_ERR_CUDA, std::string("batched Sigma: ") + cudaGetErrorString(e));
+  for (int i = 0; i < b->n; ++i) {
+    if (!split_prec(b->path[i])) continue;
+    int flag = 0;
+    if (cudaMemcpy(&flag, b->ctx[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(b, GF2_ERR_CUDA, "batched Sigma: reading an error word");
+    if (flag) return bfail(b, GF2_ERR_TIMEOUT, "instance " + std::to_string(i) + ": a pipeline wait timed out");
+  }
+  return GF2_OK;
+}

@@ -62,7 +62,7 @@ void free_all(gf2_ctx *c) {
   for (auto e : c->prof_pool) cudaEventDestroy(e);
   c->prof_recs.clear();
   c->prof_pool.clear();
-  void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_twiddle, c->d_iw_pole,
+  void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_v_split16, c->d_wt_split16, c->d_twiddle, c->d_iw_pole,
                   c->d_tau_pole, c->d_pole_resum, c->d_t2w_w, c->d_t2w_corr, c->d_ws,
                   c->d_err, c->d_small, c->d_red};
   gf2_tc_release(c);
@@ -219,7 +219,8 @@ extern "C" gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v) {
 static gf2_status sigma_dispatch(gf2_ctx *ctx, const double *d_G, int k0, int count, double *d_out, int prec) {
   if (!ctx->have_integrals) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_sigma_tau: gf2_set_integrals not called");
   if (prec == GF2_PREC_FP64) return gf2_sigma_fp64(ctx, d_G, k0, count, d_out);
-  if (prec == GF2_PREC_BF16X3 || prec == GF2_PREC_BF16X6) return gf2_sigma_tc(ctx, d_G, k0, count, d_out, prec);
+  if (prec == GF2_PREC_BF16X3 || prec == GF2_PREC_BF16X6 || prec == GF2_PREC_FP16X3 || prec == GF2_PREC_FP16X6)
+    return gf2_sigma_tc(ctx, d_G, k0, count, d_out, prec);
   return gf2_fail(ctx, GF2_ERR_ARG, "gf2_sigma_tau: unknown precision");
 }
 

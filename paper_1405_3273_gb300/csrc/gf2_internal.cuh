@@ -45,9 +45,13 @@ struct gf2_ctx {
   double *d_Wt = nullptr;   // Wt[n][p][l][j] = W[l][p][n][j] = 2 v_lpnj - v_nplj
   bool have_integrals = false;
 
-  // tensor-core operands (BF16 split planes), built by gf2_set_integrals
+  // tensor-core operands (split planes), built by gf2_set_integrals
   void *d_v_split = nullptr;    // [terms][N^4] bf16: v[i][m][q][k]
   void *d_wt_split = nullptr;   // [terms][N^4] bf16: Wt4[j][l][n][p] = W[l][p][n][j]
+  void *d_v_split16 = nullptr;  // the same as FP16 terms of 2^e_v16 v
+  void *d_wt_split16 = nullptr; // the same as FP16 terms of 2^e_w16 W
+  int e_v16 = 0, e_w16 = 0;
+  double vmax16 = 0.0;          // largest |v| after its FP16 scale
   int split_terms = 0;
 
   // grid tables (built at create)
@@ -69,6 +73,8 @@ struct gf2_ctx {
   size_t tc_ws_bytes = 0;
   int tc_chunk = 0;
   int *d_err = nullptr;           // device error word (timeouts in tcgen05 kernels)
+  bool defer_error_check = false; // set while a batch records this context into a CUDA graph:
+                                  // the split path then skips its closing read of d_err
 
   // small scratch
   double *d_small = nullptr;      // Sinv, basis(7), coef(4), misc: 16 N^2

@@ -6,7 +6,9 @@ against the oracle's FP64 Eq. Sigma (sampled points at N = 64, the full grid
 at small N through the padded path), and full GF2 energies with the split
 Sigma against the oracle.  Tolerances follow from the split arithmetic:
 two BF16 terms (three products) keep ~16 significant bits per operand, three
-terms (six products) ~24 bits, and FP32 accumulation adds ~2^-24 per sum.
+terms (six products) ~24 bits, two FP16 terms ~22 bits (three FP16 terms are
+then limited by the FP32 sums), and FP32 accumulation adds ~2^-24 per sum.
+Precision codes: 1 BF16x3, 2 BF16x6, 3 FP16x3, 4 FP16x6.
 """
 
 import ctypes
@@ -76,7 +78,7 @@ def _split_sigma(g, G, v, prec, k0=0, count=None):
         return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec,rtol", [(1, 3e-4), (2, 3e-6)])
+@pytest.mark.parametrize("prec,rtol", [(1, 3e-4), (2, 3e-6), (3, 3e-6), (4, 3e-6)])
 def test_split_sigma_padded_small_basis_full_grid(g, prec, rtol):
     """N = 10 (padded to 64 inside), 9 time points, random symmetric G and 8-fold symmetric v."""
     n, n_tau = 10, 9
@@ -87,7 +89,7 @@ def test_split_sigma_padded_small_basis_full_grid(g, prec, rtol):
     assert np.abs(got - ref).max() <= rtol * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("prec,rtol", [(1, 3e-4), (2, 5e-5)])
+@pytest.mark.parametrize("prec,rtol", [(1, 3e-4), (2, 5e-5), (3, 5e-5), (4, 5e-5)])
 def test_split_sigma_n64_sampled_points(g, prec, rtol):
     """N = 64 (no padding), 17 time points: an odd count exercises the half-empty last pair;
     the oracle evaluates three of them one by one."""
@@ -113,7 +115,7 @@ def n64_every_point_case():
     return G, v, count, osg.sigma_tau(G, v, taus=range(count))
 
 
-@pytest.mark.parametrize("prec,rtol", [(2, 3e-6), (1, 5e-5)])
+@pytest.mark.parametrize("prec,rtol", [(2, 3e-6), (1, 5e-5), (3, 3e-6), (4, 3e-6)])
 def test_split_sigma_n64_every_point_full_chunk_and_ragged_tail(g, n64_every_point_case, prec, rtol):
     """N = 64 with random symmetric G and v on a 65-point grid, the first 37 points
     in one call: one full chunk of 32 and a last chunk of 5 (padded to three pairs),
@@ -136,7 +138,7 @@ def test_split_sigma_points_offset_matches_full_grid(g):
     assert np.array_equal(full[5:12], part)
 
 
-@pytest.mark.parametrize("prec,e_tol,p_tol", [(2, 1e-6, 1e-6), (1, 1e-6, 1e-6)])
+@pytest.mark.parametrize("prec,e_tol,p_tol", [(2, 1e-6, 1e-6), (1, 1e-6, 1e-6), (3, 1e-6, 1e-6)])
 def test_split_gf2_energy_h10(g, prec, e_tol, p_tol):
     """Linear H10 (STO-3G, 1.8 bohr), beta = 100, 1025 time points, three GF2 iterations
     with the tensor-core Sigma (orthonormal basis) against the FP64 oracle: every energy
@@ -156,7 +158,7 @@ def test_split_gf2_energy_h10(g, prec, e_tol, p_tol):
     assert dp < p_tol
 
 
-@pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (1, 1e-4)])
+@pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (1, 1e-4), (3, 5e-6)])
 def test_split_sigma_physical_g_ill_conditioned_overlap(g, prec, rtol):
     """H32 2x4x4 lattice, 6-31G (cond(S) ~ 2e4): the HF Green's function near tau = 0
     has entries ~200 in the AO basis.  With the overlap given to the context the split

@@ -18,6 +18,14 @@ scaled) and a per-kernel breakdown are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x6|bf16x3|fp16x3|fp16x6]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
+  python bench.py --workload batch   # batched Sigma(tau) over 24 systems, N = 4 .. 50
+
+The batch workload has the sizes of a multi-system study: linear H_n chains,
+n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
+STO-3G lattices (N = 32), each with n_tau = 2049.  Its inputs are seeded random
+symmetric G(tau) and 8-fold-symmetric integrals of those sizes (the Sigma
+build's cost does not depend on the values); one step is one
+gf2_sigma_tau_batched call over all 24 systems (a replay of the recorded graph).
 """
 
 import argparse
@@ -53,6 +61,7 @@ def parse():
     ap.add_argument("--cpu-points", type=int, default=4, help="tau points of the oracle CPU sample")
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
+    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "batch"])
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
     args = ap.parse_args()
@@ -290,6 +299,31 @@ def run_ours(args, rank, world, dist):
                         "max_abs_dP": (P - P64).abs().max().item(), "mu_split": log[-1][1], "mu_fp64": mu64,
                         "n_split": float(torch.trace(P @ S)), "n_fp64": float(torch.trace(P64 @ S))}
 
+    # the other split precisions on the same state: Sigma build time and the same checks
+    alternates = {}
+    for name in ([] if args.no_energy_check else [x for x in ("fp16x3", "bf16x3") if x != args.prec]):
+        pc = PRECS[name]
+        g.gf2_sigma_tau(h, G_tau, Sig_new, pc)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(3):
+            a.record(stream)
+            g.gf2_sigma_tau(h, G_tau, Sig_new, pc)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        g.gf2_fft_tau_to_iw(h, Sig_new, Sig_iw, sig12)
+        Ga, Pa = torch.empty_like(G_iw), torch.empty_like(P)
+        mua, _ = g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, Ga, Pa)
+        e1, e2 = g.gf2_energy(h, hcore, F0, Pa, S, Ga, Sig_iw, sig12)
+        g.gf2_sigma_tau_points(h, G_tau, k0, cnt, outs, pc)
+        alternates[name] = {"sigma_s_per_iter": statistics.median(times) * 1e-3,
+                            "sigma_tflops_useful": flops_tau * n_tau / (statistics.median(times) * 1e-3) / 1e12,
+                            "issued_products": ISSUED[name],
+                            "split_vs_fp64_max_rel_err": ((outs - out64).abs().max() / out64.abs().max()).item(),
+                            "abs_dE_vs_fp64_gpu": abs(s.e_nuc + e1 + e2 - e64) if energy_check else None,
+                            "max_abs_dP": (Pa - P64).abs().max().item() if energy_check else None}
+
     hbm_gbs, bf16_burst, bf16_sust, peak_kind = measured_peaks()
     useful = flops_tau * n_tau
     value = useful / (ms_step * 1e-3) / 1e12 * world
@@ -370,6 +404,7 @@ def run_ours(args, rank, world, dist):
                           "split_vs_fp64_max_rel_err": rel},
         "speedup_split_vs_fp64_sigma": fp64_ms_per_tau * n_tau / sigma_ms,
         "energy_check": energy_check,
+        "alternate_precisions": alternates,
         "mu_evaluations_per_step": log[-1][2],
         "kernels": per_kernel,
         "roofline": roofline,
@@ -466,11 +501,79 @@ def run_reference(args, rank, world, dist):
     print(json.dumps(line))
 
 
+BATCH_SIZES = [4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32, 36, 40, 44, 50] + [32] * 8
+BATCH_N_TAU = 2049
+
+
+def run_batch(args, rank, world, dist):
+    """Batched Sigma(tau) over the 24 systems of the multi-system workload."""
+    import torch
+    import gf2_inputs as gi
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prec = PRECS[args.prec]
+    sizes, n_tau = BATCH_SIZES, BATCH_N_TAU
+    Gs = [torch.as_tensor(gi.random_symmetric_g(n, n_tau, seed=500 + i), device="cuda") for i, n in enumerate(sizes)]
+    outs = [torch.empty_like(x) for x in Gs]
+    useful = sum(8.0 * n ** 5 * n_tau for n in sizes)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(p, steps, warmup):
+        b = g.Batch(sizes, [n_tau] * len(sizes))
+        for i, n in enumerate(sizes):
+            g.gf2_batch_set_system(b.handle, i, torch.as_tensor(gi.random_eri(n, seed=600 + i), device="cuda"))
+        t = time.perf_counter()
+        g.gf2_batch_tune(b.handle, Gs, p)
+        tune_s = time.perf_counter() - t
+        plan = [g.gf2_batch_plan(b.handle, i) for i in range(len(sizes))]
+        for _ in range(warmup):
+            g.gf2_sigma_tau_batched(b.handle, Gs, outs, p)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a, c = ev(), ev()
+        a.record(stream)
+        for _ in range(steps):
+            g.gf2_sigma_tau_batched(b.handle, Gs, outs, p)
+        c.record(stream)
+        torch.cuda.synchronize()
+        b.close()
+        return a.elapsed_time(c) / steps, tune_s, plan
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms, tune_s, plan = timed(prec, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms64, _, _ = timed(PRECS["fp64"], 1, 1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    names = {0: "fp64", 1: "bf16x3", 2: "bf16x6", 3: "fp16x3", 4: "fp16x6"}
+    line = {"metric": "batched Σ(τ) build: useful TFLOP/s over 24 systems of uneven N", "value":
+            useful / (ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic (seeded random G(tau) and integrals)",
+            "config": {"workload": "24 systems: H_n chains n=4..50 (16) + 8 H32 lattices, STO-3G sizes, n_tau=2049",
+                       "step": "one gf2_sigma_tau_batched call (graph replay)", "parallelism": f"replicas x{world}",
+                       "l2": "inputs 1.0 GB, intermediates of the split instances several GB"},
+            "all_fp64_ms_per_step": ms64, "speedup_vs_all_fp64": ms64 / ms, "tune_s": tune_s,
+            "plan": [{"N": n, "path": names[p], "est_ms": round(e, 3), "lane": l}
+                     for n, (p, e, l) in zip(sizes, plan)],
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     rank, world, dist = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world, dist)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -7,8 +7,9 @@
 // and keeps the fastest; the FP64 path is always admissible, being the more
 // accurate.  Instances are then spread over a few worker streams by longest
 // estimated time first, and the whole batched build is recorded once into a
-// CUDA graph: a fork from the caller's stream, every instance's launches on its
-// lane, a join back.  Later calls with the same buffers replay the graph with
+// CUDA graph: a fork on a private stream of the batch, every instance's
+// launches on its lane, a join back; each replay is ordered after the caller's
+// stream and before its later work by events.  Later calls with the same buffers replay the graph with
 // one launch; the error words of the split kernels are read once afterwards.
 #include <algorithm>
 #include <new>
@@ -22,10 +23,11 @@ struct gf2_batch {
   int n = 0;
   std::vector<gf2_ctx *> ctx;
   std::vector<int> N, n_tau;
-  cudaStream_t origin = nullptr;
+  cudaStream_t origin = nullptr;  // the caller's stream (may be the legacy stream, which cannot be captured)
+  cudaStream_t cap = nullptr;     // private stream the graph is recorded on and launched on
   std::vector<cudaStream_t> lanes;
   std::vector<cudaEvent_t> ev_join;
-  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_in = nullptr, ev_out = nullptr;
   // autotuner result
   int tuned_prec = -1;
   std::vector<int> path;       // precision code each instance runs with
@@ -71,8 +73,10 @@ void release(gf2_batch *b) {
   for (auto c : b->ctx)
     if (c) gf2_destroy(c);
   for (auto s : b->lanes) cudaStreamDestroy(s);
+  if (b->cap) cudaStreamDestroy(b->cap);
   for (auto e : b->ev_join) cudaEventDestroy(e);
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (auto e : {b->ev_fork, b->ev_in, b->ev_out})
+    if (e) cudaEventDestroy(e);
 }
 
 // time one call of `prec` on instance i over `count` points from k0 (second of two calls)
@@ -106,6 +110,10 @@ extern "C" gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n
   if (!out) return GF2_ERR_ARG;
   *out = nullptr;
   if (n_inst < 1 || n_inst > 4096 || !n_bf || !n_tau) return GF2_ERR_ARG;
+  for (int i = 0; i < n_inst; ++i) {  // the gf2_create rules, checked before any context touches the device
+    const int M = n_tau[i] - 1;
+    if (n_bf[i] < 1 || n_bf[i] > GF2_MAX_N || M < 8 || M > 8192 || (M & (M - 1)) != 0) return GF2_ERR_ARG;
+  }
   gf2_batch *b = new (std::nothrow) gf2_batch();
   if (!b) return GF2_ERR_NOMEM;
   b->n = n_inst;
@@ -125,7 +133,9 @@ extern "C" gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n
     if (st == GF2_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = GF2_ERR_CUDA;
     else if (st == GF2_OK) b->ev_join.push_back(e);
   }
-  if (st == GF2_OK && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) st = GF2_ERR_CUDA;
+  for (cudaEvent_t *e : {&b->ev_fork, &b->ev_in, &b->ev_out})
+    if (st == GF2_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) st = GF2_ERR_CUDA;
+  if (st == GF2_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = GF2_ERR_CUDA;
   if (st != GF2_OK) {
     release(b);
     delete b;
@@ -240,9 +250,9 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
   if (!same) {
     drop_graph(b);
     // relaxed: the recorded calls set kernel attributes, which the stricter modes refuse
-    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
     st = e == cudaSuccess ? GF2_OK : bfail(b, GF2_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-    if (st == GF2_OK) cudaEventRecord(b->ev_fork, b->origin);
+    if (st == GF2_OK) cudaEventRecord(b->ev_fork, b->cap);
     for (size_t l = 0; l < b->lanes.size() && st == GF2_OK; ++l) {
       cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0);
       for (int i = 0; i < b->n && st == GF2_OK; ++i) {
@@ -254,10 +264,10 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
         c->defer_error_check = false;
       }
       cudaEventRecord(b->ev_join[l], b->lanes[l]);
-      cudaStreamWaitEvent(b->origin, b->ev_join[l], 0);
+      cudaStreamWaitEvent(b->cap, b->ev_join[l], 0);
     }
     cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(b->origin, &graph);
+    e = cudaStreamEndCapture(b->cap, &graph);
     if (st == GF2_OK && e != cudaSuccess)
       st = bfail(b, GF2_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     if (st == GF2_OK) {
@@ -274,8 +284,13 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
     b->graph_g.assign(d_G_tau, d_G_tau + b->n);
     b->graph_s.assign(d_Sigma_tau, d_Sigma_tau + b->n);
   }
-  cudaError_t e = cudaGraphLaunch(b->exec, b->origin);
+  // the graph runs on the private stream, after everything queued on the caller's stream
+  cudaEventRecord(b->ev_in, b->origin);
+  cudaStreamWaitEvent(b->cap, b->ev_in, 0);
+  cudaError_t e = cudaGraphLaunch(b->exec, b->cap);
   if (e != cudaSuccess) return bfail(b, GF2_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  cudaEventRecord(b->ev_out, b->cap);
+  cudaStreamWaitEvent(b->origin, b->ev_out, 0);
   if ((e = cudaStreamSynchronize(b->origin)) != cudaSuccess)
     return bfail(b, GF2_ERR_CUDA, std::string("batched Sigma: ") + cudaGetErrorString(e));
   for (int i = 0; i < b->n; ++i) {

@@ -60,3 +60,19 @@ def test_create_rejects_bad_sizes_before_touching_the_device(library):
     assert f(ctypes.byref(h), 10, 129, 64, -1.0, None) == 1       # beta < 0
     assert f(None, 10, 129, 64, 10.0, None) == 1                  # NULL out
     assert h.value is None
+
+
+def test_batch_create_rejects_bad_sizes_before_touching_the_device(library):
+    f = library.gf2_batch_create
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                  ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    ints = lambda *x: (ctypes.c_int * len(x))(*x)
+    assert f(ctypes.byref(h), 0, ints(10), ints(33), None) == 1              # no instances
+    assert f(ctypes.byref(h), 1, None, ints(33), None) == 1                  # NULL sizes
+    assert f(ctypes.byref(h), 2, ints(10, 0), ints(33, 33), None) == 1       # N = 0 in the second instance
+    assert f(None, 1, ints(10), ints(33), None) == 1                         # NULL out
+    assert h.value is None
+    assert f(ctypes.byref(h), 1, ints(10), ints(100), None) == 1             # M = 99 not a power of two
+    assert h.value is None

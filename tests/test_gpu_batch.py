@@ -1,0 +1,114 @@
+"""GPU checks of the batched Sigma entry points (gf2_batch_*, gf2_sigma_tau_batched).
+
+A batch of systems of uneven size runs through the autotuner and one recorded
+CUDA graph; every instance's Sigma(tau) is compared with the oracle's Eq. Sigma
+at the tolerance of the path the tuner chose (FP64: 1e-10 relative; FP16x3 and
+BF16x6 split: 3e-6 relative, as in the single-system split tests).  A second
+call replays the graph on new contents of the same buffers.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import gf2_inputs as gi
+from oracle import sigma as osg
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(4, 33), (10, 33), (17, 33), (40, 17), (64, 17)]   # (N, n_tau), uneven on purpose
+TOL = {0: 1e-10, 2: 3e-6, 3: 3e-6}
+
+
+@pytest.fixture(scope="module")
+def g():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import os
+    import paper_1405_3273_gb300 as g
+    from paper_1405_3273_gb300 import build
+    if not os.path.exists(g.LIB_PATH):
+        build.build()
+    g.lib()
+    return g
+
+
+@pytest.fixture(scope="module")
+def systems():
+    out = []
+    for idx, (n, n_tau) in enumerate(SIZES):
+        G = gi.random_symmetric_g(n, n_tau, seed=300 + idx)
+        v = gi.random_eri(n, seed=400 + idx)
+        out.append((G, v, osg.sigma_tau(G, v)))
+    return out
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_batched_sigma_matches_oracle_and_replays(g, systems, prec):
+    b = g.Batch([n for n, _ in SIZES], [t for _, t in SIZES])
+    try:
+        Gs = [dev(G) for G, _, _ in systems]
+        outs = [torch.zeros_like(x) for x in Gs]
+        for i, (_, v, _) in enumerate(systems):
+            g.gf2_batch_set_system(b.handle, i, dev(v))
+        g.gf2_sigma_tau_batched(b.handle, Gs, outs, prec)
+        plans = [g.gf2_batch_plan(b.handle, i) for i in range(len(SIZES))]
+        print("plan (path, est ms, lane):", plans)
+        assert all(p[0] in (0, prec) for p in plans)
+        assert plans[-1][0] == prec, "N = 64 should take the tensor-core path"
+        assert plans[0][0] == 0, "N = 4 should take the FP64 path"
+        for i, (_, _, ref) in enumerate(systems):
+            rel = np.abs(outs[i].cpu().numpy() - ref).max() / np.abs(ref).max()
+            print(f"instance {i} N={SIZES[i][0]} path {plans[i][0]}: max rel err {rel:.2e}")
+            assert rel <= TOL[plans[i][0]], i
+        # replay on new contents of the same buffers: G -> G/2 scales Sigma by 1/8
+        for x in Gs:
+            x.mul_(0.5)
+        for x in outs:
+            x.fill_(float("nan"))
+        g.gf2_sigma_tau_batched(b.handle, Gs, outs, prec)
+        for i, (_, _, ref) in enumerate(systems):
+            rel = np.abs(outs[i].cpu().numpy() - ref / 8).max() / np.abs(ref / 8).max()
+            assert rel <= TOL[plans[i][0]], i
+    finally:
+        b.close()
+
+
+def test_batched_sigma_equals_single_system_calls(g, systems):
+    """The batch runs the same kernels as gf2_sigma_tau with the tuner's path."""
+    b = g.Batch([n for n, _ in SIZES], [t for _, t in SIZES])
+    try:
+        Gs = [dev(G) for G, _, _ in systems]
+        outs = [torch.zeros_like(x) for x in Gs]
+        for i, (_, v, _) in enumerate(systems):
+            g.gf2_batch_set_system(b.handle, i, dev(v))
+        g.gf2_sigma_tau_batched(b.handle, Gs, outs, 3)
+        for i, ((n, n_tau), (G, v, _)) in enumerate(zip(SIZES, systems)):
+            path = g.gf2_batch_plan(b.handle, i)[0]
+            with g.Context(n, n_tau, 8, 1.0) as ctx:
+                g.gf2_set_integrals(ctx.handle, dev(v))
+                one = torch.zeros_like(Gs[i])
+                g.gf2_sigma_tau(ctx.handle, Gs[i], one, path)
+                torch.cuda.synchronize()
+            diff = (one - outs[i]).abs().max().item() / one.abs().max().item()
+            assert diff <= 1e-12, (i, diff)
+    finally:
+        b.close()
+
+
+def test_batched_rejects_null_buffers(g, systems):
+    b = g.Batch([4, 10], [33, 33])
+    try:
+        import ctypes
+        L = g.lib()
+        st = L.gf2_sigma_tau_batched(b.handle, None, None, 3)
+        assert st == 1
+        assert "NULL" in g.gf2_batch_last_error(b.handle)
+        with pytest.raises(g.GF2Error):
+            g.gf2_batch_tune(b.handle, [dev(systems[0][0]), dev(systems[1][0])], 3)  # no integrals yet
+        assert ctypes is not None
+    finally:
+        b.close()

@@ -14,7 +14,8 @@ Every routine follows the paper's definitions directly:
                       chemical-potential bisection;
   * ``fock``       -- Eq. FockMatrix;
   * ``energy``     -- Galitskii-Migdal energy;
+  * ``occupations`` -- natural occupation numbers eig(S^1/2 P S^1/2)/2;
   * ``gf2``        -- the self-consistent loop of the supplement (steps 1-3).
 """
 
-from . import grids, sigma, transforms, dyson, fock, energy, gf2  # noqa: F401
+from . import grids, sigma, transforms, dyson, fock, energy, gf2, occupations  # noqa: F401

@@ -13,6 +13,13 @@
 // stage removes those.  All scales are powers of two, hence exact.
 //
 // The basis is padded to NP = 64 (zero rows and columns contribute nothing).
+// For N <= 32, B = floor(64 / N) time points share one 64-wide tile: G, Gbar,
+// v and W are block-diagonal with B copies of N x N blocks (block b of G holds
+// time point b of the group), and Eq. Sigma of a block-diagonal system is the
+// block-diagonal of the per-block Sigmas -- every index of a nonzero term lies
+// in one block, since G links k-l, m-n, p-q and v, W keep i, m, q, k (and
+// l, p, n, j) in one block.  The tile pipeline is unchanged; only the splits of
+// the inputs and the output mapping know about B.
 // Per chunk of C time points three kernels run back to back:
 //
 //  sandwich   stages 1+2 fused.  Unit (tau pair, i, q pair): the v tile
@@ -199,35 +206,40 @@ __device__ __forceinline__ void split_f64(double x, uint16_t *p) {
   }
 }
 
-// Vs[t][i][q][m][k] = split_t (2^e v[i][m][q][k])  (zero outside N)
+// Vs[t][i][q][m][k] = split_t (2^e v[i][m][q][k]), block-diagonal with B
+// blocks of N (zero outside them)
 template <int F>
-__global__ void split_v_kernel(int N, const double *__restrict__ v, int e, uint16_t *__restrict__ Vs) {
+__global__ void split_v_kernel(int N, int B, const double *__restrict__ v, int e, uint16_t *__restrict__ Vs) {
   const size_t plane = (size_t)NP * NP * NP * NP;
   const double sc = ldexp(1.0, e);
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int k = idx % NP, m = (idx / NP) % NP, q = (idx / (NP * NP)) % NP, i = idx / (NP * NP * NP);
+    const int b = i / N, o = b * N;
     double x = 0.0;
-    if (i < N && m < N && q < N && k < N)
-      x = v[(((size_t)i * N + m) * N + q) * N + k] * sc;
+    if (b < B && m / N == b && q / N == b && k / N == b)
+      x = v[(((size_t)(i - o) * N + (m - o)) * N + (q - o)) * N + (k - o)] * sc;
     uint16_t p[TMAX];
     split_f64<F>(x, p);
     for (int t = 0; t < TMAX; ++t) Vs[t * plane + idx] = p[t];
   }
 }
 
-// Ws[t][j][l][n][p] = split_t (2^e W[l][p][n][j]),  W_lpnj = 2 v_lpnj - v_nplj
+// Ws[t][j][l][n][p] = split_t (2^e W[l][p][n][j]),  W_lpnj = 2 v_lpnj - v_nplj,
+// block-diagonal with B blocks of N
 template <int F>
-__global__ void split_w_kernel(int N, const double *__restrict__ v, int e, uint16_t *__restrict__ Ws) {
+__global__ void split_w_kernel(int N, int B, const double *__restrict__ v, int e, uint16_t *__restrict__ Ws) {
   const size_t plane = (size_t)NP * NP * NP * NP;
   const double sc = ldexp(1.0, e);
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int p = idx % NP, n = (idx / NP) % NP, l = (idx / (NP * NP)) % NP, j = idx / (NP * NP * NP);
+    const int bk = j / N, o = bk * N;
     double x = 0.0;
-    if (j < N && l < N && n < N && p < N) {
-      const double a = v[(((size_t)l * N + p) * N + n) * N + j];
-      const double b = v[(((size_t)n * N + p) * N + l) * N + j];
+    if (bk < B && l / N == bk && n / N == bk && p / N == bk) {
+      const int jj = j - o, ll = l - o, nn = n - o, pp = p - o;
+      const double a = v[(((size_t)ll * N + pp) * N + nn) * N + jj];
+      const double b = v[(((size_t)nn * N + pp) * N + ll) * N + jj];
       x = (2.0 * a - b) * sc;
     }
     uint16_t p3[TMAX];
@@ -247,28 +259,34 @@ __global__ void absmax_kernel(size_t n, const double *__restrict__ x, unsigned l
 
 // Gs[set][t][c][r][s]: set 0 = G(tau)^T (GT[l][k] = G[k][l]),
 //                      set 1 = Gbar = G(-tau) = -G(tau_{M-k}) (Gbar[p][q]).
-// FP16: every matrix is scaled by its own 2^ex[set][c]; block (c, 0) also sets
-// the T1 exponent ex[kExpT1][c] from the bound |T1| <= vmax_s * max_l sum_k |G_s[k][l]|
-// (vmax_s: largest |v| after its scale) and clears the T2/T3 maxima of point c.
+// Slot c holds the time points c*B + b (b < B) of the chunk in its diagonal
+// blocks of N.  FP16: every slot matrix is scaled by its own 2^ex[set][c];
+// block (c, 0) also sets the T1 exponent ex[kExpT1][c] from the bound
+// |T1| <= vmax_s * max_l sum_k |G_s[k][l]| (vmax_s: largest |v| after its
+// scale) and clears the T2/T3 maxima of slot c.
 template <int F>
-__global__ void split_g_kernel(int N, int M, int k0, int count, int C, const double *__restrict__ G,
+__global__ void split_g_kernel(int N, int B, int M, int k0, int count, int C, const double *__restrict__ G,
                                uint16_t *__restrict__ Gs, int *__restrict__ ex, double vmax_s) {
   const int c = blockIdx.x, set = blockIdx.y;
   const size_t plane = (size_t)C * NP * NP;
-  const double *src = nullptr;
-  if (c < count) src = set == 0 ? G + (size_t)(k0 + c) * N * N : G + (size_t)(M - k0 - c) * N * N;
+  auto elem = [&](int r, int s) -> double {  // entry (r, s) of the slot matrix
+    const int b = r / N;
+    if (b >= B || s / N != b || c * B + b >= count) return 0.0;
+    const int k = k0 + c * B + b, rr = r - b * N, ss = s - b * N;
+    return set == 0 ? G[(size_t)k * N * N + (size_t)ss * N + rr] : -G[(size_t)(M - k) * N * N + (size_t)rr * N + ss];
+  };
   double sc = 1.0;
   if constexpr (F != 0) {
     __shared__ double red[2][32];
-    double m = 0.0, cs = 0.0;
-    if (src) {
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) m = fmax(m, fabs(src[e]));
-      if (set == 0)
-        for (int l = threadIdx.x; l < N; l += blockDim.x) {
-          double a = 0.0;
-          for (int k = 0; k < N; ++k) a += fabs(src[(size_t)k * N + l]);
-          cs = fmax(cs, a);
-        }
+    double m = 0.0, cs = 0.0;  // largest |entry|, largest row sum of |GT| (a column sum of |G|)
+    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
+      double a = 0.0;
+      for (int q = 0; q < NP; ++q) {
+        const double x = fabs(elem(r, q));
+        a += x;
+        m = fmax(m, x);
+      }
+      cs = fmax(cs, a);
     }
     for (int o = 16; o > 0; o >>= 1) {
       m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -300,11 +318,8 @@ __global__ void split_g_kernel(int N, int M, int k0, int count, int C, const dou
     }
   }
   for (int e = threadIdx.x; e < NP * NP; e += blockDim.x) {
-    const int r = e / NP, s = e % NP;
-    double x = 0.0;
-    if (src && r < N && s < N) x = set == 0 ? src[(size_t)s * N + r] : -src[(size_t)r * N + s];
     uint16_t p[TMAX];
-    split_f64<F>(x * sc, p);
+    split_f64<F>(elem(e / NP, e % NP) * sc, p);
     for (int t = 0; t < TMAX; ++t) Gs[(size_t)(set * TMAX + t) * plane + (size_t)c * NP * NP + e] = p[t];
   }
 }
@@ -529,8 +544,8 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 template <int T, int KSUB, int F>
 __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
-                    double *__restrict__ out, int N, int count, int C, int n_units, const int *__restrict__ ex,
-                    int e_fixed, int *err) {
+                    double *__restrict__ out, int N, int B, int count, int C, int n_units,
+                    const int *__restrict__ ex, int e_fixed, int *err) {
   constexpr int SF = 4, SW = 3, SA = (T == 3) ? 3 : 4;
   constexpr uint32_t D_COLS = T * 64;  // column block b accumulates sum_a A_a W_b
   constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
@@ -659,17 +674,20 @@ __global__ void __launch_bounds__(448, 1)
         if (lane == 0) tc::mbar_arrive(d_empty);
       }
       if (!ok) break;
-      const int c = 2 * cp + row / NP, i = row % NP;
-      if (c < count && i < N) {
+      // row (slot c, i) of the tile is row i - bN of time point c B + b, b = i / N;
+      // only the columns of the same block are nonzero
+      const int c = 2 * cp + row / NP, ib = row % NP, b = ib / N, t = c * B + b;
+      if (b < B && t < count) {
         // FP16: remove the scales of v, W, G(tau) (twice), Gbar(tau) and the T3 operand
         const double unscale =
             F == 0 ? 1.0
                    : ldexp(1.0, -(e_fixed + 2 * ex[kExpG * C + c] + ex[kExpGbar * C + c] +
                                   fp16_exponent_bits(ex[kMaxT3 * C + c])));
-        double *o = out + ((size_t)c * N + i) * N + col;
+        double *o = out + ((long long)t * N + (ib - b * N)) * N + (col - b * N);
+        const int j0 = b * N - col, j1 = j0 + N;  // this thread's columns j0 <= j < j1 lie in block b
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (col + j < N) atomicAdd(o + j, -((double)hi[j] + (double)lo[j]) * unscale);
+          if (j >= j0 && j < j1) atomicAdd(o + j, -((double)hi[j] + (double)lo[j]) * unscale);
       }
     }
   } else if (warp >= 10) {
@@ -1179,11 +1197,13 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
                                    (int)sct));
   const CUtensorMap &map_v = F == 0 ? s->map_v : s->map_v16, &map_w = F == 0 ? s->map_w : s->map_w16;
   const int e_fixed = F == 0 ? 0 : ctx->e_v16 + ctx->e_w16;
-  for (int c0 = 0; c0 < count; c0 += C) {
-    const int cnt = std::min(C, count - c0);
-    const int ce = (cnt + 1) & ~1;
-    GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<F><<<dim3(C, 2), 256, 0, ctx->stream>>>(N, ctx->M, k0 + c0, cnt, C, d_G,
-                                                                                      s->Gs, s->gexp, ctx->vmax16)));
+  const int B = ctx->tc_pack;  // time points per tile slot
+  for (int c0 = 0; c0 < count; c0 += C * B) {
+    const int cnt = std::min(C * B, count - c0);
+    const int ce = (((cnt + B - 1) / B) + 1) & ~1;  // slots, rounded up to whole pairs
+    GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<F><<<dim3(C, 2), 256, 0, ctx->stream>>>(N, B, ctx->M, k0 + c0, cnt, C,
+                                                                                      d_G, s->Gs, s->gexp,
+                                                                                      ctx->vmax16)));
     GF2_CK_LAUNCH(ctx, "split_g_kernel");
     double *out = d_out + (size_t)c0 * N * N;
     GF2_CK(ctx, cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cnt * N * N, ctx->stream));
@@ -1200,7 +1220,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     const int u3 = (ce / 2) * NP;
     GF2_PROF(ctx, GF2_K_CONTRACT,
              (contract_kernel<T, kContractGroup, F><<<std::min(u3, sms), 448, sct, ctx->stream>>>(
-                 s->map_t3, map_w, out, N, cnt, C, u3, s->gexp, e_fixed, ctx->d_err)));
+                 s->map_t3, map_w, out, N, B, cnt, C, u3, s->gexp, e_fixed, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "contract_kernel");
   }
   return GF2_OK;
@@ -1213,6 +1233,7 @@ TcState *tc_state(gf2_ctx *ctx) { return reinterpret_cast<TcState *>(ctx->d_tc_w
 gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
   if (ctx->N > NP) return GF2_ERR_UNSUPPORTED;
   if (!encode_fn()) return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+  ctx->tc_pack = ctx->N <= NP / 2 ? NP / ctx->N : 1;
   const size_t bytes = TMAX * kPlane4 * sizeof(uint16_t);
   if (!ctx->d_v_split) GF2_CK(ctx, cudaMalloc(&ctx->d_v_split, bytes));
   if (!ctx->d_wt_split) GF2_CK(ctx, cudaMalloc(&ctx->d_wt_split, bytes));
@@ -1231,9 +1252,10 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
     }
     vsrc = vorth;
   }
-  split_v_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, 0, (uint16_t *)ctx->d_v_split);
+  const int B = ctx->tc_pack;
+  split_v_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, 0, (uint16_t *)ctx->d_v_split);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, 0, (uint16_t *)ctx->d_wt_split);
+  split_w_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, 0, (uint16_t *)ctx->d_wt_split);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   // FP16 planes: v scaled so that its largest entry lies in [2^13, 2^14); W
   // (|W| <= 3 max|v|) by the exponent of 3 max|v|
@@ -1250,9 +1272,9 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
   ctx->e_v16 = fp16_exponent(vmax);
   ctx->e_w16 = fp16_exponent(3.0 * vmax);
   ctx->vmax16 = ldexp(vmax, ctx->e_v16);
-  split_v_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
+  split_v_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, vsrc, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
+  split_w_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   if (vorth) {
     GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -129,6 +129,20 @@ def test_split_sigma_n64_every_point_full_chunk_and_ragged_tail(g, n64_every_poi
     assert rel.max() <= rtol
 
 
+@pytest.mark.parametrize("n,n_tau,prec,rtol", [(16, 33, 3, 3e-6), (21, 17, 3, 3e-6), (32, 17, 3, 3e-6),
+                                               (32, 17, 1, 3e-4), (13, 65, 2, 3e-6)])
+def test_split_sigma_packed_time_points(g, n, n_tau, prec, rtol):
+    """N <= 32: floor(64/N) time points share one tile as diagonal blocks (4, 3, 2, 2
+    and 4 here); every point against the oracle, including partly filled slots."""
+    G = gi.random_symmetric_g(n, n_tau, seed=40 + n)
+    v = gi.random_eri(n, seed=50 + n)
+    ref = osg.sigma_tau(G, v)
+    got = _split_sigma(g, G, v, prec)
+    rel = np.abs(got - ref).max(axis=(1, 2)) / np.abs(ref).max()
+    print(f"packed N={n} n_tau={n_tau} prec={prec}: worst point {int(rel.argmax())} at {rel.max():.2e}")
+    assert rel.max() <= rtol
+
+
 def test_split_sigma_points_offset_matches_full_grid(g):
     n, n_tau = 12, 17
     G = gi.random_symmetric_g(n, n_tau, seed=34)

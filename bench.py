@@ -19,6 +19,7 @@ scaled) and a per-kernel breakdown are reported beside it.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x6|bf16x3|fp16x3|fp16x6]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
   python bench.py --workload batch   # batched Sigma(tau) over 24 systems, N = 4 .. 50
+  python bench.py --workload h32_sto3g   # N = 32 lattice at 1.4 / 2.0 / 3.0 bohr: split vs FP64
 
 The batch workload has the sizes of a multi-system study: linear H_n chains,
 n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
@@ -61,7 +62,7 @@ def parse():
     ap.add_argument("--cpu-points", type=int, default=4, help="tau points of the oracle CPU sample")
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
-    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "batch"])
+    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "batch", "h32_sto3g"])
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
     args = ap.parse_args()
@@ -567,6 +568,77 @@ def run_batch(args, rank, world, dist):
         print(json.dumps(line))
 
 
+def run_h32_sto3g(args, rank, world, dist):
+    """H32 2x4x4 STO-3G lattice (N = 32) at three spacings: the first GF2
+    iteration from the finite-temperature HF state with the FP64 and the split
+    Sigma builds; Sigma seconds per iteration and the energy / density error of
+    each split precision against the FP64 GPU path."""
+    import torch
+    import gf2_inputs as gi
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n_tau, n_iw, beta = 4097, 8192, 100.0
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    rows = []
+    for a in (1.4, 2.0, 3.0):
+        s = gi.build_system("h32_lattice_sto3g", spacing=a)
+        r = gi.rhf(s)
+        N = s.nbf
+        ctx = g.Context(N, n_tau, n_iw, beta)
+        h = ctx.handle
+        S, hc, F0 = f64(s.S), f64(s.h), f64(r.F)
+        g.gf2_set_integrals(h, f64(s.eri))
+        g.gf2_set_overlap(h, S)
+        G_iw = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+        P = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+        mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+        mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G_iw, P)
+        mom = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+        G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+        g.gf2_tail_moments(h, S, F0, mu_hf, None, mom)
+        g.gf2_fft_iw_to_tau(h, G_iw, mom, G_tau)
+        row = {"spacing_bohr": a}
+        ref = None
+        for name in ("fp64", "bf16x3", "fp16x3", "bf16x6"):
+            pc = PRECS[name]
+            Sig = torch.empty_like(G_tau)
+            g.gf2_sigma_tau(h, G_tau, Sig, pc)
+            t0, t1 = ev(), ev()
+            torch.cuda.synchronize()
+            t0.record(stream)
+            g.gf2_sigma_tau(h, G_tau, Sig, pc)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+            sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+            g.gf2_fft_tau_to_iw(h, Sig, Sig_iw, sig12)
+            Gi, Pi = torch.empty_like(G_iw), torch.empty_like(P)
+            mu, _ = g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, Gi, Pi)
+            e1, e2 = g.gf2_energy(h, hc, F0, Pi, S, Gi, Sig_iw, sig12)
+            E = s.e_nuc + e1 + e2
+            row[name] = {"sigma_s_per_iter": t0.elapsed_time(t1) * 1e-3, "E": E}
+            if ref is None:
+                ref = (E, Pi)
+            else:
+                row[name]["abs_dE"] = abs(E - ref[0])
+                row[name]["max_abs_dP"] = (Pi - ref[1]).abs().max().item()
+        ctx.close()
+        rows.append(row)
+    worst = max(r_[p]["abs_dE"] for r_ in rows for p in ("bf16x3", "fp16x3", "bf16x6"))
+    line = {"metric": "H32 STO-3G lattice (N=32): first-iteration |ΔE| of split Σ vs FP64 GPU Σ, per spacing",
+            "value": rows[1]["fp64"]["sigma_s_per_iter"] / rows[1]["bf16x3"]["sigma_s_per_iter"],
+            "unit": "x (FP64 Σ time / BF16x3 Σ time at 2.0 bohr)", "n_gpus": world, "steps": 1,
+            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3", "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
+            "config": {"workload": "H32 2x4x4 STO-3G at 1.4/2.0/3.0 bohr, beta=100, n_tau=4097, n_iw=8192"},
+            "worst_abs_dE": worst, "spacings": rows}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     rank, world, dist = dist_setup(args.gpus)
@@ -574,6 +646,8 @@ def main():
         run_reference(args, rank, world, dist)
     elif args.workload == "batch":
         run_batch(args, rank, world, dist)
+    elif args.workload == "h32_sto3g":
+        run_h32_sto3g(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist:

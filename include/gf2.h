@@ -199,6 +199,15 @@ gf2_status gf2_combine(gf2_ctx *ctx, int n, const double *coef, const double *co
                        long long count, double *d_out);
 gf2_status gf2_gram(gf2_ctx *ctx, int n, const double *const *d_vecs, long long count, double *gram_out);
 
+/* Natural occupation numbers (the observable of the paper's H32 lattice
+ * results): d_occ[k] = k-th largest eigenvalue of S^1/2 P S^1/2, halved, i.e.
+ * the occupation of the k-th natural spatial orbital (0..1 for a physical
+ * closed-shell P; they sum to Tr(PS)/2).  d_P [N][N] spin-summed density in,
+ * d_occ [N] out.  Needs gf2_set_overlap (for S^1/2); GF2_ERR_ARG otherwise.
+ * Eigenvalues by cyclic Jacobi sweeps; GF2_ERR_NOT_CONVERGED after 60 sweeps.
+ * Synchronizes the context stream. */
+gf2_status gf2_natural_occupations(gf2_ctx *ctx, const double *d_P, double *d_occ);
+
 /* ---- Batched Eq. Sigma over many systems of uneven size ----
  * The paper builds Sigma(tau) one system at a time; the batch runs the Sigma
  * builds of many independent systems (molecules, geometries) together on one

@@ -53,6 +53,7 @@ _SIGS = {
     "gf2_combine": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.c_longlong, _P],
     "gf2_gram": [_P, _I, ctypes.POINTER(_P), ctypes.c_longlong, ctypes.POINTER(_D)],
     "gf2_energy_noalloc": [_I, _I, _D, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
+    "gf2_natural_occupations": [_P, _P, _P],
     "gf2_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
     "gf2_batch_destroy": [_P],
     "gf2_batch_last_error": [_P],
@@ -242,6 +243,10 @@ def _ptr_array(ts):
 def _check_batch(status, b):
     if status != GF2_OK:
         raise GF2Error(status, lib().gf2_batch_last_error(b).decode() if b else "")
+
+
+def gf2_natural_occupations(ctx, P, occ):
+    _check(lib().gf2_natural_occupations(ctx, _ptr(P, _F64), _ptr(occ, _F64)), ctx)
 
 
 def gf2_batch_last_error(b):

@@ -245,3 +245,25 @@ def test_h10_chain_sto3g_workload_first_iterations(library):
     e_got = np.array([e[0] for e in got.energies])
     assert np.abs(e_ref - e_got).max() < 1e-8
     assert np.abs(host(got.P) - ref.P).max() < 1e-8
+
+
+@pytest.mark.parametrize("beta", [20.0, 100.0])
+def test_natural_occupations_match_oracle_and_fermi_dirac(library, beta):
+    """H32 2x4x4 lattice, 6-31G (N = 64): occupations of a finite-temperature HF
+    density against the oracle and against the Fermi-Dirac values themselves."""
+    from oracle.occupations import natural_occupations
+    from tests import closed_forms as cf
+    s = gi.build_system("h32_lattice_631g")
+    r = gi.rhf(s)
+    mu = 0.5 * (r.eps[15] + r.eps[16])
+    _, C, _, f = cf.mo_basis(r.F, s.S, mu, beta)
+    P = cf.density_closed(C, f)
+    g = library
+    with g.Context(s.nbf, 65, 8, beta) as ctx:
+        g.gf2_set_overlap(ctx.handle, dev(s.S))
+        occ = torch.empty(s.nbf, dtype=torch.float64, device="cuda")
+        g.gf2_natural_occupations(ctx.handle, dev(P), occ)
+        got = occ.cpu().numpy()
+    assert np.abs(got - natural_occupations(P, s.S)).max() < 1e-10
+    assert np.abs(got - np.sort(f)[::-1]).max() < 1e-10
+    assert abs(got.sum() - 0.5 * np.trace(P @ s.S)) < 1e-10

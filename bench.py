@@ -149,13 +149,13 @@ def measured_peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source has not changed since it was captured."""
+def ncu_traffic(kernel, prec="bf16x6"):
+    """DRAM bytes per launch of `kernel` (captured in precision `prec`) from the
+    committed ncu summary, if the kernel source has not changed since."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(kernel)
+    d = json.load(open(p)).get(kernel if prec == "bf16x6" else f"{kernel}@{prec}")
     if not d:
         return None
     src = os.path.join(ROOT, d["source"])
@@ -371,7 +371,7 @@ def run_ours(args, rank, world, dist):
             else:
                 achieved, peak = amount / dur / 1e9, hbm_gbs
                 src = f"{peak_kind} HBM copy (MEASURED_PEAKS.json)"
-        traffic = ncu_traffic(k)
+        traffic = ncu_traffic(k, args.prec)
         r = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
              "frac": achieved / peak, "traffic": traffic, "peak_source": src, "ms_per_launch": dur * 1e3}
         if k in tensor_work:

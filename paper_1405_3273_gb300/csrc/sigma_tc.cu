@@ -68,7 +68,9 @@ constexpr uint32_t TILE64 = 64 * NP * 2;    //  8 KB: 64 rows x 64 bf16
 constexpr uint32_t kIdescKK = tc::idesc_bf16(128, 64, 0, 0);
 constexpr uint32_t kIdescMK = tc::idesc_bf16(128, 64, 1, 0);
 constexpr int kErrTimeout = 1;
-constexpr int kContractGroup = 2;  // 64-wide K steps per FP32 group in stage 4
+// 64-wide K steps per FP32 group in stage 4 (four doubled the BF16x6 error)
+template <int T>
+constexpr int contract_group() { return 2; }
 
 // product list (a, b) with a + b < T, smallest terms first
 template <int T>
@@ -279,13 +281,16 @@ __global__ void split_g_kernel(int N, int B, int M, int k0, int count, int C, co
   if constexpr (F != 0) {
     __shared__ double red[2][32];
     double m = 0.0, cs = 0.0;  // largest |entry|, largest row sum of |GT| (a column sum of |G|)
-    for (int r = threadIdx.x; r < NP; r += blockDim.x) {
+    for (int r4 = threadIdx.x; r4 < NP * 4; r4 += blockDim.x) {  // four threads per row, 16 entries each
+      const int r = r4 >> 2, q0 = (r4 & 3) * 16;
       double a = 0.0;
-      for (int q = 0; q < NP; ++q) {
+      for (int q = q0; q < q0 + 16; ++q) {
         const double x = fabs(elem(r, q));
         a += x;
         m = fmax(m, x);
       }
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
       cs = fmax(cs, a);
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -548,6 +553,8 @@ __global__ void __launch_bounds__(448, 1)
                     const int *__restrict__ ex, int e_fixed, int *err) {
   constexpr int SF = 4, SW = 3, SA = (T == 3) ? 3 : 4;
   constexpr uint32_t D_COLS = T * 64;  // column block b accumulates sum_a A_a W_b
+  // two accumulators where TMEM holds them next to the A stages (T = 2), else one
+  constexpr int DB = (2 * D_COLS + SA * T * 32 <= 512) ? 2 : 1;
   constexpr int KSTEPS = NP;  // 64-wide steps per slice of NP*NP
   constexpr int NGROUP = KSTEPS / KSUB;
   constexpr uint32_t W_STAGE = T * TILE64, A_COLS = T * 32;
@@ -557,8 +564,8 @@ __global__ void __launch_bounds__(448, 1)
   uint8_t *sW = sF + SF * kF32Tile;    // W planes
   uint64_t *bar = reinterpret_cast<uint64_t *>(sW + SW * W_STAGE);
   uint64_t *f_full = bar, *f_empty = bar + SF, *w_full = bar + 2 * SF, *w_empty = w_full + SW;
-  uint64_t *a_full = w_empty + SW, *a_empty = a_full + SA, *d_full = a_empty + SA, *d_empty = d_full + 1;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_full + 2);
+  uint64_t *a_full = w_empty + SW, *a_empty = a_full + SA, *d_full = a_empty + SA, *d_empty = d_full + DB;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(d_empty + DB);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -574,8 +581,10 @@ __global__ void __launch_bounds__(448, 1)
       tc::mbar_init(&a_full[s], 4);
       tc::mbar_init(&a_empty[s], 1);
     }
-    tc::mbar_init(d_full, 1);
-    tc::mbar_init(d_empty, 8);
+    for (int s = 0; s < DB; ++s) {
+      tc::mbar_init(&d_full[s], 1);
+      tc::mbar_init(&d_empty[s], 8);
+    }
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_t3);
@@ -584,7 +593,7 @@ __global__ void __launch_bounds__(448, 1)
   if (warp == 1) tc::tmem_alloc(tmem_slot, 512);
   __syncthreads();
   tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;  // accumulator at columns 0 .. D_COLS - 1, A stages after it
+  const uint32_t tmem = *tmem_slot;  // accumulators at columns 0 .. DB * D_COLS - 1, A stages after them
   volatile int *abort = &s_abort;
   const int npairs = n_units / NP;
 
@@ -613,8 +622,10 @@ __global__ void __launch_bounds__(448, 1)
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       for (int gi = 0; gi < NGROUP && ok; ++gi, ++grp) {
-        if (grp >= 1 && !tc::mbar_wait(d_empty, (grp - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        const int db = grp % DB;
+        if (grp >= DB && !tc::mbar_wait(&d_empty[db], ((grp / DB) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
+        const uint32_t dacc = tmem + db * D_COLS;
         for (int kq = 0; kq < KSUB; ++kq, ++g) {
           const int sa = g % SA, sw = g % SW;
           if (!tc::mbar_wait(&a_full[sa], (g / SA) & 1, abort) || !tc::mbar_wait(&w_full[sw], (g / SW) & 1, abort)) {
@@ -623,20 +634,20 @@ __global__ void __launch_bounds__(448, 1)
             break;
           }
           tc::tc_fence_after();
-          const uint32_t a0 = tmem + D_COLS + sa * A_COLS, b0 = tc::smem_u32(sW + sw * W_STAGE);
+          const uint32_t a0 = tmem + DB * D_COLS + sa * A_COLS, b0 = tc::smem_u32(sW + sw * W_STAGE);
           // A_a times the W planes 0 .. T-1-a stacked along N: columns of plane b
           // receive A_a W_b, so each block sums exactly the products a + b < T.
           // The a = 0 product spans every column and opens the group.
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t bd = tc::smem_desc(b0 + kk * 32, 16, 1024);
-            if (kq == 0 && kk == 0) tc::mma_bf16_ts(tmem, a0, bd, idesc_fmt(F, 128, T * 64, 0, 0), 0u);
+            if (kq == 0 && kk == 0) tc::mma_bf16_ts(dacc, a0, bd, idesc_fmt(F, 128, T * 64, 0, 0), 0u);
             for (int ta = T - 1; ta >= ((kq == 0 && kk == 0) ? 1 : 0); --ta)
-              tc::mma_bf16_ts(tmem, a0 + ta * 32 + kk * 8, bd, idesc_fmt(F, 128, (T - ta) * 64, 0, 0), 1u);
+              tc::mma_bf16_ts(dacc, a0 + ta * 32 + kk * 8, bd, idesc_fmt(F, 128, (T - ta) * 64, 0, 0), 1u);
           }
           tc::mma_commit(&a_empty[sa]);
           tc::mma_commit(&w_empty[sw]);
         }
-        if (ok) tc::mma_commit(d_full);
+        if (ok) tc::mma_commit(&d_full[db]);
       }
     }
   } else if (warp >= 2 && warp < 10) {
@@ -650,28 +661,35 @@ __global__ void __launch_bounds__(448, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.f;
       for (int gi = 0; gi < NGROUP; ++gi, ++grp) {
-        if (!tc::mbar_wait(d_full, grp & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        const int db = grp % DB;
+        if (!tc::mbar_wait(&d_full[db], (grp / DB) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         tc::tc_fence_after();
-        // sum the column blocks (smallest terms first), 16 columns at a time
-        const uint32_t dl = tmem + ((uint32_t)(wq * 32) << 16) + col;
+        // sum the column blocks (smallest terms first), 16 columns at a time; the
+        // T loads of a half are in flight together
+        const uint32_t dl = tmem + ((uint32_t)(wq * 32) << 16) + db * D_COLS + col;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
+          // blocks T-1 and T-2 in flight together, then (T = 3) block 0
           float v[16], w[16];
           tc::tmem_ld_32x32b_x16(dl + 64 * (T - 1) + 16 * hh, v);
+          tc::tmem_ld_32x32b_x16(dl + 64 * (T - 2) + 16 * hh, w);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int bb = T - 2; bb >= 0; --bb) {
-            tc::tmem_ld_32x32b_x16(dl + 64 * bb + 16 * hh, w);
+          for (int jj = 0; jj < 16; ++jj) v[jj] += w[jj];
+          if constexpr (T == 3) {
+            tc::tmem_ld_32x32b_x16(dl + 16 * hh, w);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj) v[jj] += w[jj];
           }
+          if (hh == 1) {  // every column of this accumulator is in registers
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&d_empty[db]);
+          }
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) two_sum_acc(hi[16 * hh + jj], lo[16 * hh + jj], v[jj]);
         }
-        tc::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(d_empty);
       }
       if (!ok) break;
       // row (slot c, i) of the tile is row i - bN of time point c B + b, b = i / N;
@@ -695,7 +713,7 @@ __global__ void __launch_bounds__(448, 1)
     // Half h of the FP32 tile holds k = 32 h .. +31 of all rows, 128 bytes a row,
     // with 16-byte chunk c of row r stored at chunk c ^ (r % 8).
     const int wq = warp & 3, r = wq * 32 + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + D_COLS;
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + DB * D_COLS;
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -748,12 +766,13 @@ __global__ void __launch_bounds__(448, 1)
 // TMEM: D1 buffers at columns 0 and 128 (128 wide), D2 buffers at 256, 320.
 // ---------------------------------------------------------------------------
 template <int T, int F>
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(448, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
                     const __grid_constant__ CUtensorMap map_t2s, int C, int n_units, int *__restrict__ ex, int *err) {
-  constexpr int GS = (T == 2) ? 2 : 1;   // buffered G sets (a tau pair each)
+  constexpr int GS = 1;                  // buffered G sets (a tau pair each; a CTA meets one or two)
   constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
   constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
+  constexpr int OS = (T == 2) ? 2 : 1;   // output staging tiles: a TMA store reads one while the next is written
   constexpr uint32_t A1_STAGE = T * TILE128, G_SET = 2 * T * TILE64, A2_BUF = T * TILE128;
   constexpr uint32_t kIdescKK128 = idesc_fmt(F, 128, 128, 0, 0), kIdescMK64 = idesc_fmt(F, 128, 64, 1, 0);
   extern __shared__ uint8_t smem_raw[];
@@ -761,12 +780,12 @@ __global__ void __launch_bounds__(320, 1)
   uint8_t *sA1 = smem;
   uint8_t *sG = sA1 + A1S * A1_STAGE;  // per set: [t][s][64][64]
   uint8_t *sA2 = sG + GS * G_SET;
-  uint8_t *sO = sA2 + A2S * A2_BUF;  // output tile [2 halves of 32 n][128 rows], 128-byte swizzle
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + kF32Tile);
+  uint8_t *sO = sA2 + A2S * A2_BUF;  // OS output tiles [2 halves of 32 n][128 rows], 128-byte swizzle
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + OS * kF32Tile);
   uint64_t *a1_full = bar, *a1_empty = bar + 2, *g_full = bar + 4, *g_empty = bar + 6;
   uint64_t *d1_full = bar + 8, *d1_empty = bar + 10, *a2_full = bar + 12, *a2_empty = bar + 14;
-  uint64_t *d2_full = bar + 16, *d2_empty = bar + 18, *o_full = bar + 20, *o_empty = bar + 21;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 22);
+  uint64_t *d2_full = bar + 16, *d2_empty = bar + 18, *o_full = bar + 20, *o_empty = bar + 22;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 24);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -776,14 +795,14 @@ __global__ void __launch_bounds__(320, 1)
       tc::mbar_init(&g_full[s], 1);
       tc::mbar_init(&g_empty[s], 1);
       tc::mbar_init(&d1_full[s], 1);
-      tc::mbar_init(&d1_empty[s], 4);
-      tc::mbar_init(&a2_full[s], 4);
+      tc::mbar_init(&d1_empty[s], 8);
+      tc::mbar_init(&a2_full[s], 8);
       tc::mbar_init(&a2_empty[s], 1);
       tc::mbar_init(&d2_full[s], 1);
       tc::mbar_init(&d2_empty[s], 4);
+      tc::mbar_init(&o_full[s], 4);
+      tc::mbar_init(&o_empty[s], 1);
     }
-    tc::mbar_init(o_full, 4);
-    tc::mbar_init(o_empty, 1);
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_v);
@@ -894,10 +913,11 @@ __global__ void __launch_bounds__(320, 1)
     }
     if (ok && pend_u >= 0 && (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)))
       raise_abort(abort, err);
-  } else if (warp >= 2 && warp < 6) {
+  } else if ((warp >= 2 && warp < 6) || warp >= 10) {
     // epilogue 1: D1[(q,m), (s,l)] -> A2_j[(q,l), m] (MN-major, 128-byte swizzle), j = 2 it + s;
-    // a warp holds 32 consecutive m of one q, so its 16-byte stores hit distinct banks
-    const int wq = warp & 3, row = wq * 32 + lane;
+    // a warp holds 32 consecutive m of one q, so its 16-byte stores hit distinct banks.
+    // Warps 2-5 convert l = 0..31, warps 10-13 l = 32..63 of the same rows.
+    const int wq = warp & 3, row = wq * 32 + lane, hf = warp >= 10 ? 1 : 0;
     const int m = row & 63, ql = row >> 6;
     int it = 0;
     bool ok = true;
@@ -908,10 +928,8 @@ __global__ void __launch_bounds__(320, 1)
       for (int s = 0; s < 2; ++s) {
         const int j = 2 * it + s;
         const float scale = F == 0 ? 1.0f : exp2_scale(ex[kExpT1 * C + 2 * cp + s]);
-        float v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + b * 128 + s * 64;
-        tc::tmem_ld_32x32b_x32(taddr, v);
-        tc::tmem_ld_32x32b_x32(taddr + 32, v + 32);
+        float v[32];
+        tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(wq * 32) << 16) + b * 128 + s * 64 + 32 * hf, v);
         tc::tmem_ld_wait();
         if (s == 1) {
           tc::tc_fence_before();
@@ -922,13 +940,14 @@ __global__ void __launch_bounds__(320, 1)
         if (j >= A2S && !tc::mbar_wait(&a2_empty[ab], ((j / A2S) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
         uint8_t *dst = sA2 + ab * A2_BUF + ql * TILE64 + m * 128;
 #pragma unroll
-        for (int cch = 0; cch < 8; ++cch) split8_store<T, F>(v + 8 * cch, dst + ((cch ^ (m & 7)) << 4), TILE128, scale);
+        for (int cch = 0; cch < 4; ++cch)
+          split8_store<T, F>(v + 8 * cch, dst + (((4 * hf + cch) ^ (m & 7)) << 4), TILE128, scale);
         tc::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&a2_full[ab]);
       }
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 6 && warp < 10) {
     // epilogue 2: D2[(q,l), n] -> T2[c][i][q][l][n]
     const int wq = warp & 3, row = wq * 32 + lane;
     int j = 0;
@@ -967,8 +986,9 @@ __global__ void __launch_bounds__(320, 1)
         }
         // row (ql, l) of the tile is row 128 qp + row of T2[c][i]; 16-byte chunk
         // k of row r in half h sits at chunk k ^ (r % 8)
-        if (j >= 1 && !tc::mbar_wait(o_empty, (j - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
-        uint8_t *orow = sO + row * 128;
+        const int ob = j % OS;
+        if (j >= OS && !tc::mbar_wait(&o_empty[ob], ((j / OS) - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        uint8_t *otile = sO + ob * kF32Tile, *orow = otile + row * 128;
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -977,15 +997,20 @@ __global__ void __launch_bounds__(320, 1)
                 make_float4(v[32 * h + 4 * k], v[32 * h + 4 * k + 1], v[32 * h + 4 * k + 2], v[32 * h + 4 * k + 3]);
         tc::fence_proxy_async_smem();  // these writes are read by the TMA store
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(o_full);
+        if (lane == 0) tc::mbar_arrive(&o_full[ob]);
         if (warp == 6) {  // the whole warp waits (uniform exit on a timeout); lane 0 issues
-          if (!tc::mbar_wait(o_full, j & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+          if (!tc::mbar_wait(&o_full[ob], (j / OS) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
           if (lane == 0) {
             const int c = 2 * cp + s;
-            for (int h = 0; h < 2; ++h) tc::tma_store_3d(&map_t2s, sO + h * (kF32Tile / 2), 32 * h, qp * 128, c * NP + i);
+            for (int h = 0; h < 2; ++h) tc::tma_store_3d(&map_t2s, otile + h * (kF32Tile / 2), 32 * h, qp * 128, c * NP + i);
             tc::tma_store_commit();
-            tc::tma_store_wait_read();
-            tc::mbar_arrive(o_empty);
+            if constexpr (OS == 1) {
+              tc::tma_store_wait_read();
+              tc::mbar_arrive(&o_empty[0]);
+            } else {  // the store of job j - 1 has read its tile once at most this one is pending
+              tc::tma_store_wait_read_but_one();
+              if (j >= 1) tc::mbar_arrive(&o_empty[(j - 1) % OS]);
+            }
           }
           __syncwarp();
         }
@@ -1179,8 +1204,8 @@ constexpr size_t kPlane4 = (size_t)NP * NP * NP * NP;
 
 template <int T>
 size_t smem_sandwich() {
-  const int GS = (T == 2) ? 2 : 1, A1S = (T == 2) ? 2 : 1, A2S = 2;
-  return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + kF32Tile + 256;
+  const int GS = 1, A1S = (T == 2) ? 2 : 1, A2S = 2, OS = (T == 2) ? 2 : 1;
+  return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + OS * kF32Tile + 256;
 }
 template <int T>
 size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }  // 4 input tiles + 1 output tile
@@ -1193,7 +1218,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
   const size_t ssw = smem_sandwich<T>(), sxf = smem_xform<T>(), sct = smem_contract<T>();
   GF2_CK(ctx, cudaFuncSetAttribute(sandwich_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssw));
   GF2_CK(ctx, cudaFuncSetAttribute(xform_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sxf));
-  GF2_CK(ctx, cudaFuncSetAttribute(contract_kernel<T, kContractGroup, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GF2_CK(ctx, cudaFuncSetAttribute(contract_kernel<T, contract_group<T>(), F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)sct));
   const CUtensorMap &map_v = F == 0 ? s->map_v : s->map_v16, &map_w = F == 0 ? s->map_w : s->map_w16;
   const int e_fixed = F == 0 ? 0 : ctx->e_v16 + ctx->e_w16;
@@ -1209,7 +1234,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     GF2_CK(ctx, cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cnt * N * N, ctx->stream));
     const int u1 = (ce / 2) * NP * 32;
     GF2_PROF(ctx, GF2_K_SANDWICH,
-             (sandwich_kernel<T, F><<<std::min(u1, sms), 320, ssw, ctx->stream>>>(map_v, s->map_g, s->map_t2s, C, u1,
+             (sandwich_kernel<T, F><<<std::min(u1, sms), 448, ssw, ctx->stream>>>(map_v, s->map_g, s->map_t2s, C, u1,
                                                                                    s->gexp, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
@@ -1219,7 +1244,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     GF2_CK_LAUNCH(ctx, "xform_kernel");
     const int u3 = (ce / 2) * NP;
     GF2_PROF(ctx, GF2_K_CONTRACT,
-             (contract_kernel<T, kContractGroup, F><<<std::min(u3, sms), 448, sct, ctx->stream>>>(
+             (contract_kernel<T, contract_group<T>(), F><<<std::min(u3, sms), 448, sct, ctx->stream>>>(
                  s->map_t3, map_w, out, N, B, cnt, C, u3, s->gexp, e_fixed, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "contract_kernel");
   }

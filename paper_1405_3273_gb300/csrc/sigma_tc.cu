@@ -347,17 +347,18 @@ __global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
                  const __grid_constant__ CUtensorMap map_t3s, int C, int n_units, int *__restrict__ ex, int *err) {
   constexpr int SF = 4, SA = 4;
+  constexpr int OS = (T == 2) ? 2 : 1;  // output staging tiles: a TMA store reads one while the next is written
   constexpr uint32_t B_SET = T * TILE64, A_COLS = T * 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *sF = smem;
   uint8_t *sB = sF + SF * kF32Tile;
-  uint8_t *sO = sB + 2 * B_SET;  // output tile [2 halves of 32 p][128 rows], 128-byte swizzle
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + kF32Tile);
+  uint8_t *sO = sB + 2 * B_SET;  // OS output tiles [2 halves of 32 p][128 rows], 128-byte swizzle
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sO + OS * kF32Tile);
   uint64_t *f_full = bar, *f_empty = bar + SF, *a_full = bar + 2 * SF, *a_empty = a_full + SA;
   uint64_t *b_full = a_empty + SA, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
-  uint64_t *o_full = b_full + 8, *o_empty = b_full + 9;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 10);
+  uint64_t *o_full = b_full + 8, *o_empty = b_full + 10;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b_full + 12);
   __shared__ int s_abort;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
@@ -374,9 +375,9 @@ __global__ void __launch_bounds__(320, 1)
       tc::mbar_init(&b_empty[s], 1);
       tc::mbar_init(&d_full[s], 1);
       tc::mbar_init(&d_empty[s], 4);
+      tc::mbar_init(&o_full[s], 4);
+      tc::mbar_init(&o_empty[s], 1);
     }
-    tc::mbar_init(o_full, 4);
-    tc::mbar_init(o_empty, 1);
     tc::fence_barrier_init();
     s_abort = 0;
     tc::prefetch_tmap(&map_t2);
@@ -467,8 +468,9 @@ __global__ void __launch_bounds__(320, 1)
           run_mx = fmaxf(run_mx, fabsf(v[k]));
         }
       }
-      if (it >= 1 && !tc::mbar_wait(o_empty, (it - 1) & 1, abort)) { raise_abort(abort, err); break; }
-      uint8_t *orow = sO + row * 128;
+      const int ob = it % OS;
+      if (it >= OS && !tc::mbar_wait(&o_empty[ob], ((it / OS) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+      uint8_t *otile = sO + ob * kF32Tile, *orow = otile + row * 128;
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -477,15 +479,20 @@ __global__ void __launch_bounds__(320, 1)
               make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2], v[32 * h + 4 * j + 3]);
       tc::fence_proxy_async_smem();  // these writes are read by the TMA store
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(o_full);
+      if (lane == 0) tc::mbar_arrive(&o_full[ob]);
       if (warp == 2) {  // the whole warp waits (uniform exit on a timeout); lane 0 issues
-        if (!tc::mbar_wait(o_full, it & 1, abort)) { raise_abort(abort, err); break; }
+        if (!tc::mbar_wait(&o_full[ob], (it / OS) & 1, abort)) { raise_abort(abort, err); break; }
         if (lane == 0) {
           for (int h = 0; h < 2; ++h)
-            tc::tma_store_3d(&map_t3s, sO + h * (kF32Tile / 2), 32 * h, mt * 128, c * NP + i);
+            tc::tma_store_3d(&map_t3s, otile + h * (kF32Tile / 2), 32 * h, mt * 128, c * NP + i);
           tc::tma_store_commit();
-          tc::tma_store_wait_read();
-          tc::mbar_arrive(o_empty);
+          if constexpr (OS == 1) {
+            tc::tma_store_wait_read();
+            tc::mbar_arrive(&o_empty[0]);
+          } else {  // the store of unit it - 1 has read its tile once at most this one is pending
+            tc::tma_store_wait_read_but_one();
+            if (it >= 1) tc::mbar_arrive(&o_empty[(it - 1) % OS]);
+          }
         }
         __syncwarp();
       }
@@ -1208,7 +1215,9 @@ size_t smem_sandwich() {
   return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + OS * kF32Tile + 256;
 }
 template <int T>
-size_t smem_xform() { return 1024 + 5 * (size_t)kF32Tile + 2 * T * TILE64 + 256; }  // 4 input tiles + 1 output tile
+size_t smem_xform() {  // 4 input tiles, B sets, 2 output tiles at T = 2 (1 at T = 3)
+  return 1024 + (4 + (T == 2 ? 2 : 1)) * (size_t)kF32Tile + 2 * T * TILE64 + 256;
+}
 template <int T>
 size_t smem_contract() { return 1024 + 4 * (size_t)kF32Tile + 3 * T * TILE64 + 256; }
 

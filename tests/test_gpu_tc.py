@@ -172,6 +172,39 @@ def test_split_gf2_energy_h10(g, prec, e_tol, p_tol):
     assert dp < p_tol
 
 
+@pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (3, 5e-6), (4, 5e-6)])
+def test_split_sigma_physical_g_mid_grid_small_magnitudes(g, prec, rtol):
+    """The same lattice at the middle of the grid, where the HF Green's function has
+    decayed to ~e^(-beta gap / 2): FP16 operands keep their bits only through the
+    per-time-point scales, which the relative error checks."""
+    from tests import closed_forms as cf
+    s = gi.build_system("h32_lattice_631g")
+    r = gi.rhf(s)
+    beta, n_tau = 100.0, 4097
+    M = n_tau - 1
+    mu = 0.5 * (r.eps[15] + r.eps[16])
+    _, C, xi, f = cf.mo_basis(r.F, s.S, mu, beta)
+    taus = np.arange(n_tau) * beta / M
+    ks = [M // 2 - 1, M // 2, M // 2 + 1]
+    G = np.zeros((n_tau, s.nbf, s.nbf))
+    for k in ks:
+        G[k] = cf.g_tau_ao(C, xi, beta, taus[[k]])[0]
+        G[M - k] = cf.g_tau_ao(C, xi, beta, taus[[M - k]])[0]
+    W = osg.exchange_combination(s.eri)
+    with g.Context(s.nbf, n_tau, 8, beta) as ctx:
+        g.gf2_set_integrals(ctx.handle, dev(s.eri))
+        g.gf2_set_overlap(ctx.handle, dev(s.S))
+        out = torch.zeros(len(ks), s.nbf, s.nbf, dtype=torch.float64, device="cuda")
+        g.gf2_sigma_tau_points(ctx.handle, dev(G), ks[0], len(ks), out, prec)
+        got = out.cpu().numpy()
+    for j, k in enumerate(ks):
+        ref = osg.sigma_factored(G[k], -G[M - k], s.eri, W)
+        rel = np.abs(got[j] - ref).max() / np.abs(ref).max()
+        print(f"mid-grid G, N=64, prec={prec}, tau index {k}: max|G|={np.abs(G[k]).max():.2e} "
+              f"max|Sigma|={np.abs(ref).max():.2e} rel err {rel:.3e}")
+        assert rel <= rtol
+
+
 @pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (1, 1e-4), (3, 5e-6)])
 def test_split_sigma_physical_g_ill_conditioned_overlap(g, prec, rtol):
     """H32 2x4x4 lattice, 6-31G (cond(S) ~ 2e4): the HF Green's function near tau = 0

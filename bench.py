@@ -92,6 +92,16 @@ def dist_setup(n):
     return rank, world, dist
 
 
+def max_over_ranks(x, dist):
+    """The largest per-rank time (the whole job is as slow as its slowest replica)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -237,10 +247,7 @@ def run_ours(args, rank, world, dist):
     ms_total = t0.elapsed_time(t1)
     ms_step = ms_total / args.steps
     sigma_ms = statistics.mean(a.elapsed_time(b) for a, b in sig_ev)
-    if dist:
-        t = torch.tensor([ms_step], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t[0])
+    ms_step = max_over_ranks(ms_step, dist)
     if args.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": ms_step, "sigma_ms": sigma_ms,
@@ -548,10 +555,7 @@ def run_batch(args, rank, world, dist):
     ms, tune_s, plan = timed(prec, args.steps, args.warmup)
     clocks = sampler.stop()
     ms64, _, _ = timed(PRECS["fp64"], 1, 1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(ms, dist)
     names = {0: "fp64", 1: "bf16x3", 2: "bf16x6", 3: "fp16x3", 4: "fp16x6"}
     line = {"metric": "batched Σ(τ) build: useful TFLOP/s over 24 systems of uneven N", "value":
             useful / (ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,

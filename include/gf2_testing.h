@@ -27,6 +27,14 @@ extern "C" {
 gf2_status gf2_test_umma_tile(int a_mn_major, const void *d_A, const void *d_B, float *d_D, int *d_err,
                               void *stream);
 
+/* Failure detection without a fault: one thread waits on an mbarrier that
+ * nothing arrives at, through the same bounded wait the tensor-core pipelines
+ * use.  After the wait limit (2 s of GPU wall time) it gives up, sets *d_err to
+ * the timeout code 1, and the kernel returns normally, leaving the CUDA context
+ * usable.  Synchronizes `stream`; GF2_ERR_ARG for a NULL d_err, GF2_ERR_CUDA if
+ * the launch fails. */
+gf2_status gf2_test_wait_timeout(int *d_err, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

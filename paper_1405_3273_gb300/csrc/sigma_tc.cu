@@ -1166,6 +1166,21 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// a wait that nothing satisfies: the bounded wait gives up and raises the error word
+__global__ void wait_timeout_kernel(int *err) {
+  __shared__ uint64_t bar;
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  volatile int *abort = &s_abort;
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, abort)) raise_abort(abort, err);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1491,6 +1506,16 @@ extern "C" gf2_status gf2_test_umma_tile(int a_mn_major, const void *d_A, const 
   if (cudaFuncSetAttribute(umma_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GF2_ERR_CUDA;
   umma_tile_kernel<<<1, 128, smem, st>>>(ma, mb, a_mn_major, d_D, d_err);
+  if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GF2_ERR_CUDA;
+  return GF2_OK;
+}
+
+// test hook: a pipeline wait that runs out (failure detection without a fault)
+extern "C" gf2_status gf2_test_wait_timeout(int *d_err, void *stream) {
+  if (!d_err) return GF2_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  wait_timeout_kernel<<<1, 32, 0, st>>>(d_err);
   if (cudaGetLastError() != cudaSuccess) return GF2_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return GF2_ERR_CUDA;
   return GF2_OK;

@@ -35,6 +35,14 @@ def test_library_exports_every_declared_symbol(library):
         assert hasattr(library, name), name
 
 
+def test_library_exports_the_test_hooks(library):
+    text = open(os.path.join(ROOT, "include", "gf2_testing.h")).read()
+    hooks = re.findall(r"^\s*gf2_status\s*(gf2_test_\w+)\s*\(", text, re.M)
+    assert sorted(hooks) == ["gf2_test_umma_tile", "gf2_test_wait_timeout"]
+    for name in hooks:
+        assert hasattr(library, name), name
+
+
 def test_binding_covers_every_declared_symbol():
     import paper_1405_3273_gb300 as g
     assert sorted(g.exported_symbols()) == declared_functions()

@@ -112,7 +112,8 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = str(device_index)
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"gf2_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

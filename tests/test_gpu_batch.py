@@ -112,3 +112,36 @@ def test_batched_rejects_null_buffers(g, systems):
         assert ctypes is not None
     finally:
         b.close()
+
+
+def test_batched_fp64_every_instance_on_the_fp64_path(g, systems):
+    """prec = FP64: the tuner has one admissible path; every instance within 1e-10 of the oracle."""
+    sizes = SIZES[:4]
+    b = g.Batch([n for n, _ in sizes], [t for _, t in sizes])
+    try:
+        Gs = [dev(G) for G, _, _ in systems[:4]]
+        outs = [torch.zeros_like(x) for x in Gs]
+        for i, (_, v, _) in enumerate(systems[:4]):
+            g.gf2_batch_set_system(b.handle, i, dev(v))
+        g.gf2_sigma_tau_batched(b.handle, Gs, outs, 0)
+        for i, (_, _, ref) in enumerate(systems[:4]):
+            assert g.gf2_batch_plan(b.handle, i)[0] == 0
+            rel = np.abs(outs[i].cpu().numpy() - ref).max() / np.abs(ref).max()
+            assert rel <= 1e-10, (i, rel)
+    finally:
+        b.close()
+
+
+def test_batch_rejects_bad_instances_and_precisions(g, systems):
+    b = g.Batch([4], [33])
+    try:
+        v = dev(systems[0][1])
+        with pytest.raises(g.GF2Error):
+            g.gf2_batch_set_system(b.handle, 1, v)          # instance out of range
+        g.gf2_batch_set_system(b.handle, 0, v)
+        with pytest.raises(g.GF2Error):
+            g.gf2_batch_tune(b.handle, [dev(systems[0][0])], 9)   # unknown precision
+        with pytest.raises(g.GF2Error):
+            g.gf2_batch_plan(b.handle, 0)                   # not tuned yet
+    finally:
+        b.close()

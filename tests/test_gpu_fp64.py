@@ -267,3 +267,11 @@ def test_natural_occupations_match_oracle_and_fermi_dirac(library, beta):
     assert np.abs(got - natural_occupations(P, s.S)).max() < 1e-10
     assert np.abs(got - np.sort(f)[::-1]).max() < 1e-10
     assert abs(got.sum() - 0.5 * np.trace(P @ s.S)) < 1e-10
+
+
+def test_natural_occupations_need_the_overlap(library):
+    g = library
+    with g.Context(6, 65, 8, 10.0) as ctx:
+        occ = torch.empty(6, dtype=torch.float64, device="cuda")
+        with pytest.raises(g.GF2Error):
+            g.gf2_natural_occupations(ctx.handle, torch.eye(6, dtype=torch.float64, device="cuda"), occ)

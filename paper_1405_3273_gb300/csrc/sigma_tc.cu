@@ -25,17 +25,19 @@
 //  sandwich   stages 1+2 fused.  Unit (tau pair, i, q pair): the v tile
 //             V[(q,m), k] (128 x 64) is loaded once and used for both time
 //             points.  MMA1  D1[(q,m), l]   = sum_k V[(q,m),k] G[k,l]
-//             (TMEM) -> split by four epilogue warps into an MN-major smem
+//             (TMEM) -> split by eight epilogue warps into an MN-major smem
 //             operand A2[(q,l), m] -> MMA2  D2[(q,l), n] = sum_m A2 G[m,n]
-//             -> four more warps store T2[tau][i][q][l][n] in FP32.
+//             -> four more warps stage T2[tau][i][q][l][n] in FP32 for TMA
+//             tile stores (two staging tiles at T = 2).
 //  xform      stage 3.  D3[(l,n), p] = sum_q T2[tau][i][q][(l,n)] Gbar[p,q]
 //             with the FP32 T2 tile read by TMA and split on chip into the
 //             MN-major bf16 operand; stores T3[tau][i][l][n][p] in FP32.
 //  contract   stage 4.  Sigma[(tau,i), j] -= sum_K T3[(tau,i), K] Wt4[j, K],
 //             K = (l,n,p) of length NP^3, rows = two time points x 64 i;
 //             T3 tiles are split on chip like T2.  Split over K in slices of
-//             NP^2 (FP32 accumulation in TMEM per slice) and reduced into the
-//             FP64 output with atomics.
+//             NP^2 (FP32 accumulation in TMEM in groups of two K steps, two
+//             accumulators at T = 2, compensated group sums) and reduced into
+//             the FP64 output with atomics.
 //
 // The intermediates T2 and T3 live in HBM as FP32 (4 bytes per value instead
 // of 2T for stored bf16 terms).  T bf16 terms of an FP32 value are formed by
@@ -768,8 +770,9 @@ __global__ void __launch_bounds__(448, 1)
 // Unit = (tau pair, i, q pair).  MMA1 covers both time points at once: its B
 // operand stacks G(tau_a)^T and G(tau_b)^T (N = 128), so D1 holds
 // [(q,m), (s,l)] for s = 0, 1.  Each half becomes one job for epilogue 1
-// (D1 -> A2 smem, MN-major) and MMA2 (N = 64, one time point); epilogue 2
-// stores each D2 tile with TMA through a swizzled shared buffer.
+// (D1 -> A2 smem, MN-major; warps 2-5 and 10-13, one column half each) and
+// MMA2 (N = 64, one time point); epilogue 2 (warps 6-9) stores each D2 tile with
+// TMA through a swizzled shared staging tile, two of them alternating at T = 2.
 // TMEM: D1 buffers at columns 0 and 128 (128 wide), D2 buffers at 256, 320.
 // ---------------------------------------------------------------------------
 template <int T, int F>

@@ -20,7 +20,7 @@ scaled) and a per-kernel breakdown are reported beside it.
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
   python bench.py --workload batch   # batched Sigma(tau) over 24 systems, N = 4 .. 50
   python bench.py --workload h32_sto3g   # N = 32 lattice at 1.4 / 2.0 / 3.0 bohr: split vs FP64
-  python bench.py --workload converge    # GF2 to convergence on the N = 64 lattice, split vs FP64
+  python bench.py --workload converge    # GF2 to convergence on the H10 chain, split vs FP64
 
 The batch workload has the sizes of a multi-system study: linear H_n chains,
 n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
     ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "batch", "h32_sto3g", "converge"])
-    ap.add_argument("--max-outer", type=int, default=12, help="outer GF2 iterations of --workload converge")
+    ap.add_argument("--max-outer", type=int, default=30, help="outer GF2 iterations of --workload converge")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
     args = ap.parse_args()
@@ -647,23 +647,25 @@ def run_h32_sto3g(args, rank, world, dist):
 
 
 def run_converge(args, rank, world, dist):
-    """Self-consistent GF2 on the N = 64 bench lattice until the energy changes by
-    less than 1e-7 Eh between outer iterations (or --max-outer), once with the
-    FP64 Sigma and once per split precision; the converged energies and densities
-    of the split runs against the FP64 run."""
+    """Self-consistent GF2 on the linear H10 chain (STO-3G, 1.8 bohr, beta = 100,
+    n_tau = 2049, n_iw = 4096) until the energy changes by less than 1e-8 Eh between
+    outer iterations (or --max-outer), once with the FP64 Sigma and once per split
+    precision; the converged energies and densities of the split runs against the
+    FP64 run, and the wall time of each run."""
     import torch
     import gf2_inputs as gi
     import paper_1405_3273_gb300 as g
     from paper_1405_3273_gb300 import driver
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    s, r = build_inputs()
+    s = gi.build_system("h10_chain_sto3g")
+    r = gi.rhf(s)
     mu0 = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
     runs = {}
-    for name in ("fp64", "fp16x3", "bf16x6"):
+    for name in ("fp64", "fp16x3", "bf16x6", "bf16x3"):
         ds = driver.to_device(s, r.F, mu0)
         t = time.perf_counter()
-        run = driver.run_gf2(ds, prec=PRECS[name], max_outer=args.max_outer, e_tol=1e-7)
+        run = driver.run_gf2(ds, prec=PRECS[name], max_outer=args.max_outer, e_tol=1e-8)
         torch.cuda.synchronize()
         runs[name] = {"seconds": time.perf_counter() - t, "energies": [e[0] for e in run.energies],
                       "P": run.P.cpu().numpy(), "mu": run.mu}
@@ -676,14 +678,12 @@ def run_converge(args, rank, world, dist):
         if name != "fp64":
             out[name]["abs_dE_final"] = abs(x["energies"][-1] - ref["energies"][-1])
             out[name]["max_abs_dP_final"] = float(np.abs(x["P"] - ref["P"]).max())
-            n = min(len(x["energies"]), len(ref["energies"]))
-            out[name]["max_abs_dE_per_iteration"] = float(max(abs(a - b) for a, b in zip(x["energies"][:n], ref["energies"][:n])))
-    line = {"metric": "converged GF2 energy, H32 2x4x4 6-31G (N=64): split Σ vs FP64 GPU Σ",
+    line = {"metric": "converged GF2 energy, linear H10 STO-3G: split Σ vs FP64 GPU Σ",
             "value": out["fp16x3"]["abs_dE_final"], "unit": "Eh (|ΔE| FP16x3 vs FP64 at convergence)",
             "n_gpus": world, "higher_is_better": False, "vs_baseline": None, "dtype": "fp16x3",
             "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
-            "config": {"workload": "H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, n_tau=4097, n_iw=8192",
-                       "stop": "|E_k - E_(k-1)| < 1e-7 Eh or max_outer"},
+            "config": {"workload": "H10 chain 1.8 bohr, STO-3G (N=10), beta=100, n_tau=2049, n_iw=4096",
+                       "stop": "|E_k - E_(k-1)| < 1e-8 Eh or max_outer"},
             "runs": out}
     if rank == 0:
         print(json.dumps(line))

@@ -73,6 +73,11 @@ constexpr int kErrTimeout = 1;
 // 64-wide K steps per FP32 group in stage 4 (four doubled the BF16x6 error)
 template <int T>
 constexpr int contract_group() { return 2; }
+// stage-4 ring depths (32 KB T3 tiles, T x 8 KB W stages) within 227 KB of shared memory
+template <int T>
+constexpr int contract_stages_f() { return T == 2 ? 5 : 4; }
+template <int T>
+constexpr int contract_stages_w() { return 4; }
 
 // product list (a, b) with a + b < T, smallest terms first
 template <int T>
@@ -560,7 +565,10 @@ __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
                     double *__restrict__ out, int N, int B, int count, int C, int n_units,
                     const int *__restrict__ ex, int e_fixed, int *err) {
-  constexpr int SF = 4, SW = 3, SA = (T == 3) ? 3 : 4;
+  // T3 tile and W stages: the producer is held back by whichever ring frees last,
+  // and a W stage is released only when the MMA of its K step is done, so the
+  // W ring must be as deep as the T3 ring for the HBM loads to run ahead
+  constexpr int SF = contract_stages_f<T>(), SW = contract_stages_w<T>(), SA = (T == 3) ? 3 : 4;
   constexpr uint32_t D_COLS = T * 64;  // column block b accumulates sum_a A_a W_b
   // two accumulators where TMEM holds them next to the A stages (T = 2), else one
   constexpr int DB = (2 * D_COLS + SA * T * 32 <= 512) ? 2 : 1;
@@ -1237,7 +1245,9 @@ size_t smem_xform() {  // 4 input tiles, B sets, 2 output tiles at T = 2 (1 at T
   return 1024 + (4 + (T == 2 ? 2 : 1)) * (size_t)kF32Tile + 2 * T * TILE64 + 256;
 }
 template <int T>
-size_t smem_contract() { return 1024 + 4 * (size_t)kF32Tile + 3 * T * TILE64 + 256; }
+size_t smem_contract() {
+  return 1024 + contract_stages_f<T>() * (size_t)kF32Tile + contract_stages_w<T>() * T * TILE64 + 256;
+}
 
 template <int T, int F>
 gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int count, double *d_out) {

@@ -61,10 +61,12 @@ typedef enum {
  *   GF2_PREC_BF16X6  three BF16 terms, six products (i + j <= 2).
  *   GF2_PREC_FP16X3  two FP16 terms, three products.  FP16 has three more
  *                    significand bits than BF16 but a narrow exponent range, so
- *                    v and W carry one power-of-two scale each, every G(tau)
- *                    and G(-tau) its own (largest entry in [2^13, 2^14)), and
- *                    each intermediate is scaled by 2^-20 before it is split;
- *                    the scales are powers of two and are removed exactly.
+ *                    every FP16 operand carries a power-of-two scale that puts
+ *                    its largest entry in [2^13, 2^14): one for v, one for W,
+ *                    one per G(tau) and per G(-tau), and per time point for
+ *                    each intermediate (from a bound for the first, from the
+ *                    measured maximum for the other two); the scales are
+ *                    removed exactly.
  *   GF2_PREC_FP16X6  three FP16 terms, six products, the same scaling. */
 typedef enum {
   GF2_PREC_FP64 = 0,
@@ -89,7 +91,8 @@ const char *gf2_last_error(const gf2_ctx *ctx);
 
 /* Copy the two-electron integrals v [N^4] into the context and build the
  * exchange combination W_lpnj = 2 v_lpnj - v_nplj of Eq. Sigma plus its BF16
- * split copies for the tensor-core path. */
+ * and FP16 split copies for the tensor-core path (for N <= 32 as floor(64/N)
+ * diagonal blocks, so that several time points share one 64-wide tile). */
 gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v);
 
 /* Give the context the overlap S [N][N] (symmetric positive definite).  The

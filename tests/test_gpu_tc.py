@@ -172,6 +172,39 @@ def test_split_gf2_energy_h10(g, prec, e_tol, p_tol):
     assert dp < p_tol
 
 
+@pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (3, 5e-6), (1, 1e-4)])
+def test_split_sigma_physical_g_packed_sto3g_lattice(g, prec, rtol):
+    """H32 2x4x4 STO-3G lattice at 3.0 bohr (N = 32: two time points per tile) with the
+    overlap given (Loewdin basis): the HF Green's function at the first grid points and
+    at the middle of the grid, every point against the oracle."""
+    from tests import closed_forms as cf
+    s = gi.build_system("h32_lattice_sto3g", spacing=3.0)
+    r = gi.rhf(s)
+    beta, n_tau = 100.0, 4097
+    M = n_tau - 1
+    mu = 0.5 * (r.eps[15] + r.eps[16])
+    _, C, xi, f = cf.mo_basis(r.F, s.S, mu, beta)
+    taus = np.arange(n_tau) * beta / M
+    G = np.zeros((n_tau, s.nbf, s.nbf))
+    W = osg.exchange_combination(s.eri)
+    with g.Context(s.nbf, n_tau, 8, beta) as ctx:
+        g.gf2_set_integrals(ctx.handle, dev(s.eri))
+        g.gf2_set_overlap(ctx.handle, dev(s.S))
+        for k0 in (1, M // 2 - 2):
+            ks = list(range(k0, k0 + 5))
+            for k in ks:
+                G[k] = cf.g_tau_ao(C, xi, beta, taus[[k]])[0]
+                G[M - k] = cf.g_tau_ao(C, xi, beta, taus[[M - k]])[0]
+            out = torch.zeros(len(ks), s.nbf, s.nbf, dtype=torch.float64, device="cuda")
+            g.gf2_sigma_tau_points(ctx.handle, dev(G), ks[0], len(ks), out, prec)
+            got = out.cpu().numpy()
+            for j, k in enumerate(ks):
+                ref = osg.sigma_factored(G[k], -G[M - k], s.eri, W)
+                rel = np.abs(got[j] - ref).max() / np.abs(ref).max()
+                print(f"packed STO-3G lattice, prec={prec}, tau index {k}: rel err {rel:.3e}")
+                assert rel <= rtol, k
+
+
 @pytest.mark.parametrize("prec,rtol", [(2, 5e-6), (3, 5e-6), (4, 5e-6)])
 def test_split_sigma_physical_g_mid_grid_small_magnitudes(g, prec, rtol):
     """The same lattice at the middle of the grid, where the HF Green's function has

@@ -90,11 +90,13 @@ def _diis_coefficients(gram):
     return np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
 
 
-def inner_loop(run, tol=1e-8, max_iter=200, mu_tol=1e-10, diis=8):
+def inner_loop(run, tol=1e-8, max_iter=300, mu_tol=1e-10, diis=8, mix=0.5, diis_from=1e-3):
     """Steps 2.a-2.b: mu search and Fock rebuild until the Fock residual
-    R = F(P(F)) - F has Frobenius norm below ``tol``; the next F is the Pulay
-    extrapolation of the last ``diis`` rebuilt matrices.  G, P and mu are
-    re-evaluated at the converged F."""
+    R = F(P(F)) - F has Frobenius norm below ``tol``.  Far from the fixed point
+    (|R| > ``diis_from``) the next F is the damped step F + mix R; closer in it is
+    the Pulay (DIIS) extrapolation of the last ``diis`` rebuilt matrices.  (From
+    the HF state of a correlated lattice the fixed point can sit 20 mEh away in
+    mu, where DIIS alone wanders.)  G, P and mu are re-evaluated at the converged F."""
     s = run.sys
     h = run.ctx.handle
     hist_F, hist_R = [], []
@@ -106,23 +108,27 @@ def inner_loop(run, tol=1e-8, max_iter=200, mu_tol=1e-10, diis=8):
         gf2_fock(h, s.h, run.P, F_out)
         R = torch.empty_like(run.F)
         gf2_combine(h, [1.0, -1.0], [F_out, run.F], R)
-        if gf2_gram(h, [R])[0][0] ** 0.5 < tol:
+        r_norm = gf2_gram(h, [R])[0][0] ** 0.5
+        if r_norm < tol:
             run.F = F_out
             run.mu, nev = gf2_mu_search(h, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
                                         run.G_iw, run.P, tol=mu_tol)
             run.mu_evals.append(nev)
             return
-        if diis > 0:
-            hist_F.append(F_out)
-            hist_R.append(R)
-            hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
-            if len(hist_F) > 1:
-                c = _diis_coefficients(gf2_gram(h, hist_R))
-                F_next = torch.empty_like(run.F)
-                gf2_combine(h, list(c), hist_F, F_next)
-                run.F = F_next
-            else:
-                run.F = F_out
+        if r_norm > diis_from or diis <= 0:
+            hist_F, hist_R = [], []
+            F_next = torch.empty_like(run.F)
+            gf2_combine(h, [1.0, mix], [run.F, R], F_next)
+            run.F = F_next
+            continue
+        hist_F.append(F_out)
+        hist_R.append(R)
+        hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
+        if len(hist_F) > 1:
+            c = _diis_coefficients(gf2_gram(h, hist_R))
+            F_next = torch.empty_like(run.F)
+            gf2_combine(h, list(c), hist_F, F_next)
+            run.F = F_next
         else:
             run.F = F_out
     raise RuntimeError("inner loop did not converge")

@@ -568,8 +568,8 @@ def run_batch(args, rank, world, dist):
                        "step": "one gf2_sigma_tau_batched call (graph replay)", "parallelism": f"replicas x{world}",
                        "l2": "inputs 1.0 GB, intermediates of the split instances several GB"},
             "all_fp64_ms_per_step": ms64, "speedup_vs_all_fp64": ms64 / ms, "tune_s": tune_s,
-            "plan": [{"N": n, "path": names[p], "est_ms": round(e, 3), "lane": l}
-                     for n, (p, e, l) in zip(sizes, plan)],
+            "plan": [{"N": n, "path": names[p], "est_ms": round(e, 3), "lane": l, "slots_per_launch": c}
+                     for n, (p, e, l, c) in zip(sizes, plan)],
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

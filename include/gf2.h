@@ -221,13 +221,16 @@ gf2_status gf2_natural_occupations(gf2_ctx *ctx, const double *d_P, double *d_oc
  *   gf2_batch_set_system: integrals v [N^4] of an instance (copied) and its
  *     overlap S [N][N] (may be NULL: no orthogonalisation, as gf2_set_overlap).
  *   gf2_batch_tune: autotuner.  For every instance it times each admissible
- *     path on one chunk of 32 points of d_G_tau[i] -- the FP64 staged
- *     contraction, and for N <= 64 the split tensor-core pipeline in `prec` --
- *     keeps the fastest (FP64 is always admissible, being more accurate), and
+ *     path on a sample of d_G_tau[i] -- the FP64 staged contraction (32
+ *     points), and for N <= 64 the split tensor-core pipeline in `prec` with
+ *     32 or 16 time-point slots per launch (one chunk each) -- keeps the
+ *     fastest (FP64 is always admissible, being more accurate), and
  *     spreads the instances over the worker streams, longest estimated time
  *     first.  d_G_tau: host array of n_inst device pointers [n_tau[i]][N][N].
  *   gf2_batch_plan: the tuner's choice for one instance: precision code it
- *     runs with, estimated ms of one full-grid build, worker stream index.
+ *     runs with, estimated ms of one full-grid build, worker stream index,
+ *     time-point slots per launch of the split pipeline (32 or 16).  Any
+ *     output pointer may be NULL.
  *   gf2_sigma_tau_batched: d_Sigma_tau[i] [n_tau[i]][N][N] <- Eq. Sigma of
  *     instance i from d_G_tau[i] (host arrays of device pointers).  Tunes first
  *     if `prec` differs from the last tuning.  The first call with a given set
@@ -243,7 +246,7 @@ gf2_status gf2_batch_destroy(gf2_batch *b);
 const char *gf2_batch_last_error(const gf2_batch *b);
 gf2_status gf2_batch_set_system(gf2_batch *b, int inst, const double *d_v, const double *d_S);
 gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau, int prec);
-gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane);
+gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane, int *chunk);
 gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, double *const *d_Sigma_tau,
                                  int prec);
 

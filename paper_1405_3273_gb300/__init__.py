@@ -59,7 +59,7 @@ _SIGS = {
     "gf2_batch_last_error": [_P],
     "gf2_batch_set_system": [_P, _I, _P, _P],
     "gf2_batch_tune": [_P, ctypes.POINTER(_P), _I],
-    "gf2_batch_plan": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)],
+    "gf2_batch_plan": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "gf2_sigma_tau_batched": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I],
     "gf2_profile": [_P, _I],
     "gf2_profile_report": [_P, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong)],
@@ -276,10 +276,12 @@ def gf2_batch_tune(b, G_taus, prec):
 
 
 def gf2_batch_plan(b, inst):
-    """(precision code, estimated ms per full-grid build, worker stream) chosen for an instance."""
-    p, ms, lane = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
-    _check_batch(lib().gf2_batch_plan(b, int(inst), ctypes.byref(p), ctypes.byref(ms), ctypes.byref(lane)), b)
-    return p.value, ms.value, lane.value
+    """(precision code, estimated ms per full-grid build, worker stream, slots per
+    split-pipeline launch) chosen for an instance."""
+    p, ms, lane, chunk = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    _check_batch(lib().gf2_batch_plan(b, int(inst), ctypes.byref(p), ctypes.byref(ms), ctypes.byref(lane),
+                                      ctypes.byref(chunk)), b)
+    return p.value, ms.value, lane.value, chunk.value
 
 
 def gf2_sigma_tau_batched(b, G_taus, Sigma_taus, prec):

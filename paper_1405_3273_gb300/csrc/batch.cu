@@ -1,16 +1,17 @@
 // Eq. Sigma for a batch of independent systems of uneven size on one GPU.
 //
 // Each instance keeps its own context (integrals, split planes, workspace).
-// An autotuner times the candidate paths of every instance on one chunk of
-// its own time grid -- the FP64 staged contraction on the CUDA cores, and the
-// split tensor-core pipeline (padded to 64 basis functions) when N <= 64 --
-// and keeps the fastest; the FP64 path is always admissible, being the more
-// accurate.  Instances are then spread over a few worker streams by longest
-// estimated time first, and the whole batched build is recorded once into a
-// CUDA graph: a fork on a private stream of the batch, every instance's
-// launches on its lane, a join back; each replay is ordered after the caller's
-// stream and before its later work by events.  Later calls with the same buffers replay the graph with
-// one launch; the error words of the split kernels are read once afterwards.
+// An autotuner times the candidate paths of every instance on a sample of its
+// own time grid -- the FP64 staged contraction on the CUDA cores, and the split
+// tensor-core pipeline (64-wide tiles, time points packed for N <= 32) with 32
+// or 16 time-point slots per launch when N <= 64 -- and keeps the fastest; the
+// FP64 path is always admissible, being the more accurate.  Instances are then
+// spread over a few worker streams by longest estimated time first, and the
+// whole batched build is recorded once into a CUDA graph: a fork on a private
+// stream of the batch, every instance's launches on its lane, a join back; each
+// replay is ordered after the caller's stream and before its later work by
+// events.  Later calls with the same buffers replay the graph with one launch;
+// the error words of the split kernels are read once afterwards.
 #include <algorithm>
 #include <new>
 #include <numeric>
@@ -31,6 +32,7 @@ struct gf2_batch {
   // autotuner result
   int tuned_prec = -1;
   std::vector<int> path;       // precision code each instance runs with
+  std::vector<int> chunk;      // split pipeline: time-point slots per launch
   std::vector<double> est_ms;  // estimated ms of one full-grid Sigma build
   std::vector<int> lane_of;
   // recorded graph and the buffers it was recorded with
@@ -177,39 +179,62 @@ extern "C" gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau,
   }
   drop_graph(b);
   b->path.assign(b->n, GF2_PREC_FP64);
+  b->chunk.assign(b->n, 32);
   b->est_ms.assign(b->n, 0.0);
   b->lane_of.assign(b->n, 0);
-  // one chunk of the split pipeline (32 points) is the sample for every candidate
+  // the sample: 32 points for FP64, one chunk (up to 32 slots of tc_pack points) for the split pipeline
   size_t out_elems = 0;
-  for (int i = 0; i < b->n; ++i) out_elems = std::max(out_elems, (size_t)32 * b->N[i] * b->N[i]);
+  for (int i = 0; i < b->n; ++i)
+    out_elems = std::max(out_elems, (size_t)std::min(b->n_tau[i], 32 * std::max(1, b->ctx[i]->tc_pack)) *
+                                        b->N[i] * b->N[i]);
   double *d_out = nullptr;
   if (cudaMalloc(&d_out, out_elems * sizeof(double)) != cudaSuccess)
     return bfail(b, GF2_ERR_NOMEM, "gf2_batch_tune: sample buffer");
   gf2_status st = GF2_OK;
   for (int i = 0; i < b->n && st == GF2_OK; ++i) {
     const int count = std::min(32, b->n_tau[i]);
-    std::vector<int> cands{GF2_PREC_FP64};
-    if (split_prec(prec) && b->N[i] <= kTcMaxN) cands.push_back(prec);
+    gf2_ctx *c = b->ctx[i];
+    // candidates: FP64, and the split pipeline with 32 or 16 slots per launch
+    // (16 halves its 4.3 GB of intermediates and doubles its launches)
+    struct Cand { int prec, chunk; };
+    std::vector<Cand> cands{{GF2_PREC_FP64, 32}};
+    if (split_prec(prec) && b->N[i] <= kTcMaxN) {
+      cands.push_back({prec, 32});
+      cands.push_back({prec, 16});
+    }
     double best = 0.0;
-    for (int p : cands) {
+    for (size_t k = 0; k < cands.size() && st == GF2_OK; ++k) {
+      const Cand cd = cands[k];
+      if (cd.prec != GF2_PREC_FP64) {  // a fresh workspace of this chunk size
+        if (cudaStreamSynchronize(b->origin) != cudaSuccess) st = bfail(b, GF2_ERR_CUDA, "autotuner: sync");
+        gf2_tc_release(c);
+        c->tc_chunk_max = cd.chunk;
+      }
+      // one whole chunk of this candidate
+      const int cnt = std::min(b->n_tau[i], cd.prec == GF2_PREC_FP64 ? count : cd.chunk * c->tc_pack);
       double ms = 0.0;
-      if ((st = time_path(b, i, d_G_tau[i], d_out, 0, count, p, &ms)) != GF2_OK) break;
-      const double full = ms * b->n_tau[i] / count;
-      if (p == cands.front() || full < best) {
+      if (st == GF2_OK && (st = time_path(b, i, d_G_tau[i], d_out, 0, cnt, cd.prec, &ms)) != GF2_OK) break;
+      const double full = ms * b->n_tau[i] / cnt;
+      if (k == 0 || full < best) {
         best = full;
-        b->path[i] = p;
+        b->path[i] = cd.prec;
+        b->chunk[i] = cd.chunk;
       }
     }
     b->est_ms[i] = best;
-    // keep only the workspace of the chosen path (a split chunk holds 4.3 GB of intermediates)
-    gf2_ctx *c = b->ctx[i];
+    if (st != GF2_OK) break;
+    // keep only the workspace of the chosen path and chunk size, allocated now:
+    // the graph recording that follows must not allocate
     if (cudaStreamSynchronize(b->origin) != cudaSuccess) st = bfail(b, GF2_ERR_CUDA, "autotuner: sync");
-    if (b->path[i] == GF2_PREC_FP64) {
-      gf2_tc_release(c);
-    } else if (c->d_ws) {
-      cudaFree(c->d_ws);
-      c->d_ws = nullptr;
-      c->ws_elems = 0;
+    gf2_tc_release(c);
+    c->tc_chunk_max = b->chunk[i];
+    if (st == GF2_OK && b->path[i] != GF2_PREC_FP64) {
+      if (c->d_ws) {
+        cudaFree(c->d_ws);
+        c->d_ws = nullptr;
+        c->ws_elems = 0;
+      }
+      st = from_ctx(b, i, gf2_sigma_tau_points(c, d_G_tau[i], 0, std::min(b->n_tau[i], 2), d_out, b->path[i]));
     }
   }
   cudaFree(d_out);
@@ -228,9 +253,11 @@ extern "C" gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau,
   return GF2_OK;
 }
 
-extern "C" gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane) {
+extern "C" gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane,
+                                     int *chunk) {
   if (!b || inst < 0 || inst >= b->n || b->tuned_prec < 0) return GF2_ERR_ARG;
   if (path) *path = b->path[inst];
+  if (chunk) *chunk = b->chunk[inst];
   if (est_ms) *est_ms = b->est_ms[inst];
   if (lane) *lane = b->lane_of[inst];
   return GF2_OK;

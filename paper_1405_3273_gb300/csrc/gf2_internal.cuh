@@ -72,6 +72,7 @@ struct gf2_ctx {
   void *d_tc_ws = nullptr;
   size_t tc_ws_bytes = 0;
   int tc_chunk = 0;
+  int tc_chunk_max = 32;           // slots per split-pipeline launch (even, 2..32; the batch tuner sets it)
   int tc_pack = 1;                // time points per 64-wide tile slot (floor(64/N) for N <= 32)
   int *d_err = nullptr;           // device error word (timeouts in tcgen05 kernels)
   bool defer_error_check = false; // set while a batch records this context into a CUDA graph:

@@ -1350,7 +1350,7 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
   if (ctx->d_tc_ws) return GF2_OK;
   TcState *s = new (std::nothrow) TcState();
   if (!s) return gf2_fail(ctx, GF2_ERR_NOMEM, "tc state");
-  s->C = std::max(2, std::min(32, ((ctx->n_tau + 1) / 2) * 2));
+  s->C = std::max(2, std::min(ctx->tc_chunk_max, ((ctx->n_tau + 1) / 2) * 2));
   const int C = s->C;
   const size_t gbytes = (size_t)2 * TMAX * C * NP * NP * sizeof(uint16_t);
   const size_t ibytes = (size_t)C * kPlane4 * sizeof(float);

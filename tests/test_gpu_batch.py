@@ -56,7 +56,8 @@ def test_batched_sigma_matches_oracle_and_replays(g, systems, prec):
             g.gf2_batch_set_system(b.handle, i, dev(v))
         g.gf2_sigma_tau_batched(b.handle, Gs, outs, prec)
         plans = [g.gf2_batch_plan(b.handle, i) for i in range(len(SIZES))]
-        print("plan (path, est ms, lane):", plans)
+        print("plan (path, est ms, lane, slots per launch):", plans)
+        assert all(p[3] in (16, 32) for p in plans)
         assert all(p[0] in (0, prec) for p in plans)
         assert plans[-1][0] == prec, "N = 64 should take the tensor-core path"
         # (for N = 4 the two paths take about the same time; either choice is valid)

@@ -354,13 +354,16 @@ __global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
                  const __grid_constant__ CUtensorMap map_t3s, int C, int n_units, int *__restrict__ ex, int *err) {
   constexpr int SF = 4, SA = 4;
-  constexpr int OS = (T == 2) ? 2 : 1;  // output staging tiles: a TMA store reads one while the next is written
+  constexpr int OS = 2;  // output staging tiles: a TMA store reads one while the next is written
+  // Gbar sets: two at T = 2; one at T = 3, where the room goes to the second
+  // staging tile (a CTA's contiguous block of units meets one or two time points)
+  constexpr int GB = (T == 2) ? 2 : 1;
   constexpr uint32_t B_SET = T * TILE64, A_COLS = T * 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
   uint8_t *sF = smem;
   uint8_t *sB = sF + SF * kF32Tile;
-  uint8_t *sO = sB + 2 * B_SET;  // OS output tiles [2 halves of 32 p][128 rows], 128-byte swizzle
+  uint8_t *sO = sB + GB * B_SET;  // OS output tiles [2 halves of 32 p][128 rows], 128-byte swizzle
   uint64_t *bar = reinterpret_cast<uint64_t *>(sO + OS * kF32Tile);
   uint64_t *f_full = bar, *f_empty = bar + SF, *a_full = bar + 2 * SF, *a_empty = a_full + SA;
   uint64_t *b_full = a_empty + SA, *b_empty = b_full + 2, *d_full = b_full + 4, *d_empty = b_full + 6;
@@ -396,15 +399,18 @@ __global__ void __launch_bounds__(320, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
+  // a contiguous block of units per CTA (balanced to within one unit)
+  const int u_begin = (int)((long long)blockIdx.x * n_units / gridDim.x);
+  const int u_end = (int)((long long)(blockIdx.x + 1) * n_units / gridDim.x);
 
   if (warp == 0 && lane == 0) {
     const uint64_t stream_pol = tc::policy_evict_first();
     int it = 0, cur_c = -1, gcount = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end; ++u, ++it) {
       const int c = u / (NP * 32), i = (u / 32) % NP, mt = u % 32;
       if (c != cur_c) {
-        const int gs = gcount & 1;
-        if (gcount >= 2 && !tc::mbar_wait(&b_empty[gs], ((gcount >> 1) - 1) & 1, abort)) { raise_abort(abort, err); break; }
+        const int gs = gcount % GB;
+        if (gcount >= GB && !tc::mbar_wait(&b_empty[gs], ((gcount / GB) - 1) & 1, abort)) { raise_abort(abort, err); break; }
         tc::mbar_arrive_expect_tx(&b_full[gs], B_SET);
         for (int t = 0; t < T; ++t)
           tc::tma_load_3d(sB + gs * B_SET + t * TILE64, &map_g, &b_full[gs], 0, 0, (TMAX + t) * C + c);
@@ -418,12 +424,12 @@ __global__ void __launch_bounds__(320, 1)
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0, gs = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end; ++u, ++it) {
       const int c = u / (NP * 32);
       if (c != cur_c) {
         if (cur_c >= 0) tc::mma_commit(&b_empty[gs]);
-        gs = gcount & 1;
-        if (!tc::mbar_wait(&b_full[gs], (gcount >> 1) & 1, abort)) { raise_abort(abort, err); break; }
+        gs = gcount % GB;
+        if (!tc::mbar_wait(&b_full[gs], (gcount / GB) & 1, abort)) { raise_abort(abort, err); break; }
         cur_c = c;
         ++gcount;
       }
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(320, 1)
     int it = 0;
     float run_mx = 0.f;  // FP16: largest |T3| of time point run_c seen by this thread
     int run_c = -1;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end; ++u, ++it) {
       const int c = u / (NP * 32), i = (u / 32) % NP, mt = u % 32;
       const int d = it & 1;
       if (!tc::mbar_wait(&d_full[d], (it >> 1) & 1, abort)) { raise_abort(abort, err); break; }
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(320, 1)
     const int wq = warp & 3, m = wq * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16) + 128;
     int it = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int u = u_begin; u < u_end; ++u, ++it) {
       const int s = it % SF, sa = it % SA;
       const float scale = F == 0 ? 1.0f : exp2_scale(fp16_exponent_bits(ex[kMaxT2 * C + u / (NP * 32)]));
       if (!tc::mbar_wait(&f_full[s], (it / SF) & 1, abort)) { raise_abort(abort, err); break; }
@@ -1241,8 +1247,8 @@ size_t smem_sandwich() {
   return 1024 + A1S * T * TILE128 + GS * 2 * T * TILE64 + A2S * T * TILE128 + OS * kF32Tile + 256;
 }
 template <int T>
-size_t smem_xform() {  // 4 input tiles, B sets, 2 output tiles at T = 2 (1 at T = 3)
-  return 1024 + (4 + (T == 2 ? 2 : 1)) * (size_t)kF32Tile + 2 * T * TILE64 + 256;
+size_t smem_xform() {  // 4 input tiles, 2 output tiles, Gbar sets (two at T = 2, one at T = 3)
+  return 1024 + 6 * (size_t)kF32Tile + (T == 2 ? 2 : 1) * T * TILE64 + 256;
 }
 template <int T>
 size_t smem_contract() {

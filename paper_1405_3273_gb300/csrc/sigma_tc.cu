@@ -352,7 +352,8 @@ __global__ void split_g_kernel(int N, int B, int M, int k0, int count, int C, co
 template <int T, int F>
 __global__ void __launch_bounds__(320, 1)
     xform_kernel(const __grid_constant__ CUtensorMap map_t2, const __grid_constant__ CUtensorMap map_g,
-                 const __grid_constant__ CUtensorMap map_t3s, int C, int n_units, int *__restrict__ ex, int *err) {
+                 const __grid_constant__ CUtensorMap map_t3s, int C, int S, int sl0, int n_units, int *__restrict__ ex,
+                 int *err) {
   constexpr int SF = 4, SA = 4;
   constexpr int OS = 2;  // output staging tiles: a TMA store reads one while the next is written
   // Gbar sets: two at T = 2; one at T = 3, where the room goes to the second
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(320, 1)
         if (gcount >= GB && !tc::mbar_wait(&b_empty[gs], ((gcount / GB) - 1) & 1, abort)) { raise_abort(abort, err); break; }
         tc::mbar_arrive_expect_tx(&b_full[gs], B_SET);
         for (int t = 0; t < T; ++t)
-          tc::tma_load_3d(sB + gs * B_SET + t * TILE64, &map_g, &b_full[gs], 0, 0, (TMAX + t) * C + c);
+          tc::tma_load_3d(sB + gs * B_SET + t * TILE64, &map_g, &b_full[gs], 0, 0, (TMAX + t) * S + sl0 + c);
         cur_c = c;
         ++gcount;
       }
@@ -469,9 +470,9 @@ __global__ void __launch_bounds__(320, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&d_empty[d]);
       if constexpr (F != 0) {  // remove the T2 operand scale; record max |T3| of the time point
-        const float un = exp2_scale(-fp16_exponent_bits(ex[kMaxT2 * C + c]));
+        const float un = exp2_scale(-fp16_exponent_bits(ex[kMaxT2 * S + sl0 + c]));
         if (c != run_c) {  // one atomic per warp and time point, not per unit
-          if (run_c >= 0) warp_absmax_to(&ex[kMaxT3 * C + run_c], run_mx);
+          if (run_c >= 0) warp_absmax_to(&ex[kMaxT3 * S + sl0 + run_c], run_mx);
           run_c = c;
           run_mx = 0.f;
         }
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(320, 1)
         __syncwarp();
       }
     }
-    if (F != 0 && run_c >= 0) warp_absmax_to(&ex[kMaxT3 * C + run_c], run_mx);
+    if (F != 0 && run_c >= 0) warp_absmax_to(&ex[kMaxT3 * S + sl0 + run_c], run_mx);
     if (warp == 2 && lane == 0) tc::tma_store_wait_all();
   } else if (warp >= 6) {
     // converter: row m = 32 (warp % 4) + lane of the tile, the TMEM lane this warp may access
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(320, 1)
     int it = 0;
     for (int u = u_begin; u < u_end; ++u, ++it) {
       const int s = it % SF, sa = it % SA;
-      const float scale = F == 0 ? 1.0f : exp2_scale(fp16_exponent_bits(ex[kMaxT2 * C + u / (NP * 32)]));
+      const float scale = F == 0 ? 1.0f : exp2_scale(fp16_exponent_bits(ex[kMaxT2 * S + sl0 + u / (NP * 32)]));
       if (!tc::mbar_wait(&f_full[s], (it / SF) & 1, abort)) { raise_abort(abort, err); break; }
       float x[64];
       const float *src = reinterpret_cast<const float *>(sF + s * kF32Tile) + m;
@@ -569,7 +570,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
 template <int T, int KSUB, int F>
 __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
-                    double *__restrict__ out, int N, int B, int count, int C, int n_units,
+                    double *__restrict__ out, int N, int B, int count, int C, int S, int sl0, int n_units,
                     const int *__restrict__ ex, int e_fixed, int *err) {
   // T3 tile and W stages: the producer is held back by whichever ring frees last,
   // and a W stage is released only when the MMA of its K step is done, so the
@@ -722,8 +723,8 @@ __global__ void __launch_bounds__(448, 1)
         // FP16: remove the scales of v, W, G(tau) (twice), Gbar(tau) and the T3 operand
         const double unscale =
             F == 0 ? 1.0
-                   : ldexp(1.0, -(e_fixed + 2 * ex[kExpG * C + c] + ex[kExpGbar * C + c] +
-                                  fp16_exponent_bits(ex[kMaxT3 * C + c])));
+                   : ldexp(1.0, -(e_fixed + 2 * ex[kExpG * S + sl0 + c] + ex[kExpGbar * S + sl0 + c] +
+                                  fp16_exponent_bits(ex[kMaxT3 * S + sl0 + c])));
         double *o = out + ((long long)t * N + (ib - b * N)) * N + (col - b * N);
         const int j0 = b * N - col, j1 = j0 + N;  // this thread's columns j0 <= j < j1 lie in block b
 #pragma unroll
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(448, 1)
     bool ok = true;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const int c = 2 * (u % npairs) + r / NP;
-      const float scale = F == 0 ? 1.0f : exp2_scale(fp16_exponent_bits(ex[kMaxT3 * C + c]));
+      const float scale = F == 0 ? 1.0f : exp2_scale(fp16_exponent_bits(ex[kMaxT3 * S + sl0 + c]));
       for (int ks = 0; ks < KSTEPS; ++ks, ++g) {
         const int s = g % SF, sa = g % SA;
         if (!tc::mbar_wait(&f_full[s], (g / SF) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
@@ -792,7 +793,8 @@ __global__ void __launch_bounds__(448, 1)
 template <int T, int F>
 __global__ void __launch_bounds__(448, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
-                    const __grid_constant__ CUtensorMap map_t2s, int C, int n_units, int *__restrict__ ex, int *err) {
+                    const __grid_constant__ CUtensorMap map_t2s, int C, int S, int sl0, int n_units,
+                    int *__restrict__ ex, int *err) {
   constexpr int GS = 1;                  // buffered G sets (a tau pair each; a CTA meets one or two)
   constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
   constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
@@ -854,7 +856,7 @@ __global__ void __launch_bounds__(448, 1)
         for (int t = 0; t < T; ++t)
           for (int s = 0; s < 2; ++s)
             tc::tma_load_3d(sG + gs * G_SET + (t * 2 + s) * TILE64, &map_g, &g_full[gs], 0, 0,
-                            t * C + 2 * cp + s);
+                            t * S + sl0 + 2 * cp + s);
         cur_cp = cp;
         ++gcount;
       }
@@ -951,7 +953,7 @@ __global__ void __launch_bounds__(448, 1)
       tc::tc_fence_after();
       for (int s = 0; s < 2; ++s) {
         const int j = 2 * it + s;
-        const float scale = F == 0 ? 1.0f : exp2_scale(ex[kExpT1 * C + 2 * cp + s]);
+        const float scale = F == 0 ? 1.0f : exp2_scale(ex[kExpT1 * S + sl0 + 2 * cp + s]);
         float v[32];
         tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(wq * 32) << 16) + b * 128 + s * 64 + 32 * hf, v);
         tc::tmem_ld_wait();
@@ -982,7 +984,7 @@ __global__ void __launch_bounds__(448, 1)
       const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
       if (F != 0 && cp != run_cp) {  // one atomic per warp and time point, not per job
         if (run_cp >= 0)
-          for (int s = 0; s < 2; ++s) warp_absmax_to(&ex[kMaxT2 * C + 2 * run_cp + s], run_mx[s]);
+          for (int s = 0; s < 2; ++s) warp_absmax_to(&ex[kMaxT2 * S + sl0 + 2 * run_cp + s], run_mx[s]);
         run_cp = cp;
         run_mx[0] = run_mx[1] = 0.f;
       }
@@ -999,7 +1001,7 @@ __global__ void __launch_bounds__(448, 1)
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&d2_empty[b]);
         if constexpr (F != 0) {  // remove the T1 operand scale; record max |T2| of the time point
-          const float un = exp2_scale(-ex[kExpT1 * C + 2 * cp + s]);
+          const float un = exp2_scale(-ex[kExpT1 * S + sl0 + 2 * cp + s]);
           float mx = run_mx[s];
 #pragma unroll
           for (int k = 0; k < 64; ++k) {
@@ -1041,7 +1043,7 @@ __global__ void __launch_bounds__(448, 1)
       }
     }
     if (F != 0 && run_cp >= 0)
-      for (int s = 0; s < 2; ++s) warp_absmax_to(&ex[kMaxT2 * C + 2 * run_cp + s], run_mx[s]);
+      for (int s = 0; s < 2; ++s) warp_absmax_to(&ex[kMaxT2 * S + sl0 + 2 * run_cp + s], run_mx[s]);
     if (warp == 6 && lane == 0) tc::tma_store_wait_all();
   }
   __syncthreads();
@@ -1231,9 +1233,10 @@ bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, 
 }
 
 struct TcState {
-  int C = 0;
-  uint16_t *Gs = nullptr;              // split G sets (BF16 or FP16 bits)
-  int *gexp = nullptr;                 // [kExpSets][C] FP16 scale exponents and maxima per time point
+  int C = 0;                           // slots per chunk (one launch of each tile kernel)
+  int S = 0;                           // slots of the whole grid (a multiple of C)
+  uint16_t *Gs = nullptr;              // split G sets of every slot of the grid (BF16 or FP16 bits)
+  int *gexp = nullptr;                 // [kExpSets][S] FP16 scale exponents and maxima per slot
   float *T2 = nullptr, *T3 = nullptr;  // FP32 intermediates, C * NP^4 each
   CUtensorMap map_v, map_g, map_t2, map_t2s, map_t3, map_t3s, map_w;
   CUtensorMap map_v16, map_w16;        // the FP16 planes of v and W
@@ -1266,29 +1269,32 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
   const CUtensorMap &map_v = F == 0 ? s->map_v : s->map_v16, &map_w = F == 0 ? s->map_w : s->map_w16;
   const int e_fixed = F == 0 ? 0 : ctx->e_v16 + ctx->e_w16;
   const int B = ctx->tc_pack;  // time points per tile slot
-  for (int c0 = 0; c0 < count; c0 += C * B) {
+  const int S = s->S;          // slot stride of the split G planes and the exponents
+  if (count <= 0) return GF2_OK;
+  // every slot of the call split in one launch, the whole output cleared once
+  const int n_chunks = (count + C * B - 1) / (C * B);
+  GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<F><<<dim3(n_chunks * C, 2), 256, 0, ctx->stream>>>(
+                                 N, B, ctx->M, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
+  GF2_CK_LAUNCH(ctx, "split_g_kernel");
+  GF2_CK(ctx, cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)count * N * N, ctx->stream));
+  for (int c0 = 0, sl0 = 0; c0 < count; c0 += C * B, sl0 += C) {
     const int cnt = std::min(C * B, count - c0);
     const int ce = (((cnt + B - 1) / B) + 1) & ~1;  // slots, rounded up to whole pairs
-    GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<F><<<dim3(C, 2), 256, 0, ctx->stream>>>(N, B, ctx->M, k0 + c0, cnt, C,
-                                                                                      d_G, s->Gs, s->gexp,
-                                                                                      ctx->vmax16)));
-    GF2_CK_LAUNCH(ctx, "split_g_kernel");
     double *out = d_out + (size_t)c0 * N * N;
-    GF2_CK(ctx, cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cnt * N * N, ctx->stream));
     const int u1 = (ce / 2) * NP * 32;
     GF2_PROF(ctx, GF2_K_SANDWICH,
-             (sandwich_kernel<T, F><<<std::min(u1, sms), 448, ssw, ctx->stream>>>(map_v, s->map_g, s->map_t2s, C, u1,
-                                                                                   s->gexp, ctx->d_err)));
+             (sandwich_kernel<T, F><<<std::min(u1, sms), 448, ssw, ctx->stream>>>(map_v, s->map_g, s->map_t2s, C, S, sl0,
+                                                                                   u1, s->gexp, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
     GF2_PROF(ctx, GF2_K_XFORM,
-             (xform_kernel<T, F><<<std::min(u2, sms), 320, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->map_t3s, C, u2,
-                                                                               s->gexp, ctx->d_err)));
+             (xform_kernel<T, F><<<std::min(u2, sms), 320, sxf, ctx->stream>>>(s->map_t2, s->map_g, s->map_t3s, C, S, sl0,
+                                                                               u2, s->gexp, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "xform_kernel");
     const int u3 = (ce / 2) * NP;
     GF2_PROF(ctx, GF2_K_CONTRACT,
              (contract_kernel<T, contract_group<T>(), F><<<std::min(u3, sms), 448, sct, ctx->stream>>>(
-                 s->map_t3, map_w, out, N, B, cnt, C, u3, s->gexp, e_fixed, ctx->d_err)));
+                 s->map_t3, map_w, out, N, B, cnt, C, S, sl0, u3, s->gexp, e_fixed, ctx->d_err)));
     GF2_CK_LAUNCH(ctx, "contract_kernel");
   }
   return GF2_OK;
@@ -1358,11 +1364,15 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
   if (!s) return gf2_fail(ctx, GF2_ERR_NOMEM, "tc state");
   s->C = std::max(2, std::min(ctx->tc_chunk_max, ((ctx->n_tau + 1) / 2) * 2));
   const int C = s->C;
-  const size_t gbytes = (size_t)2 * TMAX * C * NP * NP * sizeof(uint16_t);
+  // slots of the whole grid, rounded up to whole chunks
+  const int B = ctx->tc_pack;
+  s->S = ((((ctx->n_tau + B - 1) / B) + C - 1) / C) * C;
+  const int S = s->S;
+  const size_t gbytes = (size_t)2 * TMAX * S * NP * NP * sizeof(uint16_t);
   const size_t ibytes = (size_t)C * kPlane4 * sizeof(float);
   cudaError_t e = cudaMalloc(&s->Gs, gbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&s->gexp, kExpSets * C * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->gexp, 0, kExpSets * C * sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&s->gexp, kExpSets * S * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->gexp, 0, kExpSets * S * sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = cudaMalloc(&s->T2, ibytes);
   if (e == cudaSuccess) e = cudaMalloc(&s->T3, ibytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->T2, 0, ibytes, ctx->stream);
@@ -1383,8 +1393,8 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
     ok &= make_map(&s->map_v, ctx->d_v_split, 5, dims, str, box);
     ok &= make_map(&s->map_v16, ctx->d_v_split16, 5, dims, str, box);
   }
-  {  // G sets: dims (64, 64, 2*TMAX*C), box (64, 64, 1)
-    uint64_t dims[3] = {NP, NP, (uint64_t)2 * TMAX * C};
+  {  // G sets of every slot: dims (64, 64, 2*TMAX*S), box (64, 64, 1)
+    uint64_t dims[3] = {NP, NP, (uint64_t)2 * TMAX * S};
     uint64_t str[2] = {NP * 2, NP * NP * 2};
     uint32_t box[3] = {64, 64, 1};
     ok &= make_map(&s->map_g, s->Gs, 3, dims, str, box);

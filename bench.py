@@ -419,7 +419,12 @@ def run_ours(args, rank, world, dist):
                    "l2": "inputs larger than L2 (G(iw) 537 MB, intermediates 6 GB)",
                    "parallelism": f"replicas x{world}"},
         "sigma": {"s_per_iter": sigma_ms * 1e-3, "tflops_useful": sigma_tflops,
-                  "tensor_kernels_ms": tc_ms, "tflops_issued": sigma_tflops * issued_factor},
+                  "tensor_kernels_ms": tc_ms, "tflops_issued": sigma_tflops * issued_factor,
+                  # split products issued against the sustained BF16 peak: over the whole
+                  # build (including its FP64 basis transforms) and over the three tensor kernels
+                  "issued_frac_of_bf16_build": sigma_tflops * issued_factor / bf16_sust,
+                  "issued_frac_of_bf16_tensor_kernels": (useful * issued_factor / (tc_ms * 1e-3) / 1e12 / bf16_sust
+                                                         if tc_ms > 0 else None)},
         "fp64_gpu_path": {"sigma_s_per_iter": fp64_ms_per_tau * 1e-3 * n_tau,
                           "tflops": flops_tau / (fp64_ms_per_tau * 1e-3) / 1e12,
                           "sample": f"{cnt} tau points from k={k0}",

@@ -1314,45 +1314,72 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
   if (!ctx->d_v_split16) GF2_CK(ctx, cudaMalloc(&ctx->d_v_split16, bytes));
   if (!ctx->d_wt_split16) GF2_CK(ctx, cudaMalloc(&ctx->d_wt_split16, bytes));
   const int blocks = 8 * ctx->num_sms;
-  // integrals in the orthonormal (Loewdin) basis when the overlap is known
-  double *vsrc = ctx->d_v, *vorth = nullptr;
+  // With the overlap known the contraction runs in the orthonormal (Loewdin)
+  // basis: v' = (S^-1/2)^{x4} v, G' = S^1/2 G S^1/2.  Of the back transform
+  // Sigma = S^1/2 Sigma' S^1/2 the right factor (Sigma's column index j) is
+  // folded into W: vw = v' x_4 S^1/2 and W = 2 vw_lpnj - vw_nplj, so the tile
+  // kernels return Sigma' S^1/2 and one FP64 product per time point supplies
+  // the left factor.  (Folding the left factor into v as well saved 3.6 ms more
+  // but raised the energy error three- to fourfold: measured.)
+  const int N = ctx->N;
+  const size_t n4 = (size_t)N * N * N * N;
+  double *vs = ctx->d_v, *vw = ctx->d_v, *vorth = nullptr, *vfold = nullptr;
   if (ctx->d_Shalf) {
-    const size_t n4 = (size_t)ctx->N * ctx->N * ctx->N * ctx->N;
     GF2_CK(ctx, cudaMalloc(&vorth, n4 * sizeof(double)));
-    gf2_status st = gf2_orth_transform_v(ctx, vorth);
-    if (st != GF2_OK) {
+    if (cudaMalloc(&vfold, n4 * sizeof(double)) != cudaSuccess) {
       cudaFree(vorth);
+      return gf2_fail(ctx, GF2_ERR_NOMEM, "gf2_set_integrals: folded integrals");
+    }
+    gf2_status st = gf2_orth_transform_v(ctx, vorth);
+    const long long N3 = (long long)N * N * N;
+    if (st == GF2_OK) {  // vw[(l,p,n), b] = sum_j v'[(l,p,n), j] Sh[j, b]
+      Dgemm g{};
+      g.M = (int)N3; g.N = N; g.K = N;
+      g.A = vorth; g.a_rs = N; g.a_cs = 1;
+      g.B = ctx->d_Shalf; g.b_rs = N; g.b_cs = 1;
+      g.C = vfold; g.c_rs = N; g.c_cs = 1;
+      g.nb0 = 1; g.nb1 = 1; g.alpha = 1.0; g.beta_c = 0.0; g.split_k = 1;
+      st = gf2_dgemm(ctx, g);
+    }
+    if (st != GF2_OK) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(vorth);
+      cudaFree(vfold);
       return st;
     }
-    vsrc = vorth;
+    vs = vorth;
+    vw = vfold;
   }
   const int B = ctx->tc_pack;
-  split_v_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, 0, (uint16_t *)ctx->d_v_split);
+  split_v_kernel<0><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, 0, (uint16_t *)ctx->d_v_split);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<0><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, 0, (uint16_t *)ctx->d_wt_split);
+  split_w_kernel<0><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, 0, (uint16_t *)ctx->d_wt_split);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   // FP16 planes: v scaled so that its largest entry lies in [2^13, 2^14); W
-  // (|W| <= 3 max|v|) by the exponent of 3 max|v|
-  const size_t n4 = (size_t)ctx->N * ctx->N * ctx->N * ctx->N;
+  // (|W| <= 3 max|vw|) by the exponent of 3 max|vw|
   unsigned long long *d_amax = reinterpret_cast<unsigned long long *>(ctx->d_red);
-  GF2_CK(ctx, cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), ctx->stream));
-  absmax_kernel<<<blocks, 256, 0, ctx->stream>>>(n4, vsrc, d_amax);
+  GF2_CK(ctx, cudaMemsetAsync(d_amax, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  absmax_kernel<<<blocks, 256, 0, ctx->stream>>>(n4, vs, d_amax);
   GF2_CK_LAUNCH(ctx, "absmax_kernel");
-  unsigned long long bits = 0;
-  GF2_CK(ctx, cudaMemcpyAsync(&bits, d_amax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+  absmax_kernel<<<blocks, 256, 0, ctx->stream>>>(n4, vw, d_amax + 1);
+  GF2_CK_LAUNCH(ctx, "absmax_kernel");
+  unsigned long long bits[2] = {0, 0};
+  GF2_CK(ctx, cudaMemcpyAsync(bits, d_amax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
   GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
-  double vmax;
-  std::memcpy(&vmax, &bits, sizeof(vmax));
+  double vmax, wmax;
+  std::memcpy(&vmax, &bits[0], sizeof(vmax));
+  std::memcpy(&wmax, &bits[1], sizeof(wmax));
   ctx->e_v16 = fp16_exponent(vmax);
-  ctx->e_w16 = fp16_exponent(3.0 * vmax);
+  ctx->e_w16 = fp16_exponent(3.0 * wmax);
   ctx->vmax16 = ldexp(vmax, ctx->e_v16);
-  split_v_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
+  split_v_kernel<1><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<1><<<blocks, 256, 0, ctx->stream>>>(ctx->N, B, vsrc, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
+  split_w_kernel<1><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   if (vorth) {
     GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(vorth);
+    cudaFree(vfold);
   }
   ctx->split_terms = TMAX;
   return GF2_OK;
@@ -1464,7 +1491,8 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, doub
   if (st != GF2_OK) return st;
   GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   TcState *s = tc_state(ctx);
-  // in the orthonormal basis: G' = S^{1/2} G S^{1/2} in, Sigma = S^{1/2} Sigma' S^{1/2} out
+  // in the orthonormal basis: G' = S^{1/2} G S^{1/2} in; the kernels write
+  // Sigma' S^{1/2} (the right factor is folded into W), the left factor follows
   const double *G_use = d_G;
   double *out_use = d_out;
   if (ctx->d_Shalf) {
@@ -1480,7 +1508,19 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, doub
     default: st = run_chunks<3, 1>(ctx, s, G_use, k0, count, out_use); break;
   }
   if (st != GF2_OK) return st;
-  if (ctx->d_Shalf && (st = gf2_orth_sigma_to_ao(ctx, out_use, count, d_out)) != GF2_OK) return st;
+  if (ctx->d_Shalf) {  // the row index: Sigma[b] = S^1/2 X[b]
+    const long long N2 = (long long)ctx->N * ctx->N;
+    for (int b0 = 0; b0 < count; b0 += 65535) {
+      const int nb = std::min(65535, count - b0);
+      Dgemm g{};
+      g.M = ctx->N; g.N = ctx->N; g.K = ctx->N;
+      g.A = ctx->d_Shalf; g.a_rs = ctx->N; g.a_cs = 1; g.a_b0 = 0;
+      g.B = out_use + b0 * N2; g.b_rs = ctx->N; g.b_cs = 1; g.b_b0 = N2;
+      g.C = d_out + b0 * N2; g.c_rs = ctx->N; g.c_cs = 1; g.c_b0 = N2;
+      g.nb0 = nb; g.nb1 = 1; g.alpha = 1.0; g.beta_c = 0.0; g.split_k = 1;
+      if ((st = gf2_dgemm(ctx, g)) != GF2_OK) return st;
+    }
+  }
   // Eq. Sigma is symmetric; the two triangles carry independent rounding of the
   // split arithmetic, and their average is the better estimate
   if ((st = gf2_symmetrize(ctx, d_out, count)) != GF2_OK) return st;

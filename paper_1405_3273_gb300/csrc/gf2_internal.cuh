@@ -146,7 +146,6 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, 
 gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx);
 void gf2_tc_release(gf2_ctx *ctx);
 gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int count, double **d_Gorth);
-gf2_status gf2_orth_sigma_to_ao(gf2_ctx *ctx, const double *d_Sig_orth, int count, double *d_out);
 gf2_status gf2_orth_transform_v(gf2_ctx *ctx, double *d_vorth);
 gf2_status gf2_symmetrize(gf2_ctx *ctx, double *d_X, int count);
 

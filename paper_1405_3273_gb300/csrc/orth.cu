@@ -180,14 +180,6 @@ gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int cou
   return GF2_OK;
 }
 
-// Sigma_AO = S^{1/2} Sigma' S^{1/2} for `count` matrices
-gf2_status gf2_orth_sigma_to_ao(gf2_ctx *ctx, const double *d_Sig_orth, int count, double *d_out) {
-  const long long N2 = (long long)ctx->N * ctx->N;
-  const size_t grid = (size_t)ctx->n_tau * N2;
-  double *tmp = ctx->d_orth_ws + grid;
-  return sandwich_batch(ctx, ctx->d_Shalf, d_Sig_orth, ctx->d_Shalf, tmp, d_out, count);
-}
-
 namespace {
 // X <- (X + X^T)/2 for `count` N x N matrices
 __global__ void symmetrize_kernel(int N, long long count, double *X) {

@@ -9,8 +9,10 @@
 // transforms themselves are FP64 (CUDA cores): S^{1/2} and S^{-1/2} by the
 // coupled Newton-Schulz iteration (Y -> (S/c)^{1/2}, Z -> (S/c)^{-1/2},
 // T = (3I - ZY)/2, Y <- YT, Z <- TZ, c = ||S||_F so that the spectrum of S/c
-// lies in (0, 1]), v by four single-index transforms, G and Sigma by two
-// matrix products per time point.
+// lies in (0, 1]), v by four single-index transforms, G by two matrix
+// products per time point.  Of Sigma's back transform, the split path folds
+// the right factor into its W operand and applies the left one as a single
+// FP64 product per time point.
 #include <algorithm>
 #include <cmath>
 

@@ -78,7 +78,7 @@ typedef enum {
 
 typedef struct gf2_ctx gf2_ctx;
 
-/* Create a context for N basis functions (1 <= N <= 112), n_tau time points
+/* Create a context for N basis functions (1 <= N <= 128), n_tau time points
  * (M = n_tau - 1 a power of two, 8 <= M <= 16384), n_iw >= 1 Matsubara
  * frequencies and inverse temperature
  * beta > 0, bound to the CUDA stream `stream` (a cudaStream_t; NULL = legacy
@@ -214,7 +214,7 @@ gf2_status gf2_natural_occupations(gf2_ctx *ctx, const double *d_P, double *d_oc
 /* ---- Batched Eq. Sigma over many systems of uneven size ----
  * The paper builds Sigma(tau) one system at a time; the batch runs the Sigma
  * builds of many independent systems (molecules, geometries) together on one
- * GPU.  Instance i has n_bf[i] basis functions (1..112) and n_tau[i] time
+ * GPU.  Instance i has n_bf[i] basis functions (1..128) and n_tau[i] time
  * points (the gf2_create rules).  Every instance owns a context; the batch
  * also creates up to four worker streams that fork from and join back into
  * `stream` (a cudaStream_t, NULL = legacy default stream).
@@ -256,9 +256,9 @@ gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, dou
  * running while a CUDA graph is captured, inside host callbacks, or in hosts
  * that give the library a fixed memory budget and forbid the device
  * allocator.  Its scratch (per-frequency partial sums, S^-1, the results) is
- * a fixed __device__ array of 65536 + 112*112 + 8 doubles (about 610 KB) that
+ * a fixed __device__ array of 65536 + 128*128 + 8 doubles (about 655 KB) that
  * every device loading the library keeps until the process exits.
- *   Limits: n_bf <= 112 and n_iw <= 65536, else GF2_ERR_UNSUPPORTED before any
+ *   Limits: n_bf <= 128 and n_iw <= 65536, else GF2_ERR_UNSUPPORTED before any
  *   launch; NULL pointers or bad sizes give GF2_ERR_ARG; CUDA failures
  *   GF2_ERR_CUDA.  d_sig12 may be NULL (no tail term).
  *   The first call on a device looks up the array's device address (once per

@@ -637,7 +637,7 @@ extern "C" gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *
 
 namespace {
 
-constexpr int kNoallocMaxN = GF2_MAX_N;                 // 112
+constexpr int kNoallocMaxN = GF2_MAX_N;                 // 128
 constexpr int kNoallocMaxIw = 65536;
 constexpr size_t kNoallocDoubles = (size_t)kNoallocMaxIw + (size_t)kNoallocMaxN * kNoallocMaxN + 8;
 

@@ -11,7 +11,7 @@
 // Real pole (hartree) about which the four-moment tail is resummed:
 // T(z) = sum_r c_r (z - a)^-r with the moments G1..G4 of Eq. GF.
 #define GF2_TAIL_POLE 1.0
-#define GF2_MAX_N 112
+#define GF2_MAX_N 128
 
 // slots of ctx->d_small, each N*N doubles
 enum {

@@ -3,7 +3,7 @@
 //
 // X = S^1/2 P S^1/2 by two FP64 GEMMs, then the eigenvalues of the symmetric
 // N x N matrix by the cyclic Jacobi method in one CTA, the matrix resident in
-// shared memory (N <= 112: 100 KB).  Each sweep visits every pair (p, q) once
+// shared memory (N <= 128: 130 KB).  Each sweep visits every pair (p, q) once
 // in N' - 1 rounds of the round-robin ordering (N' = N rounded up to even):
 // the pairs of a round are disjoint, so their rotations commute and are applied
 // together -- all row updates, then all column updates.  Rotation per Golub &

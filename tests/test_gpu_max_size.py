@@ -1,11 +1,11 @@
 """GPU parity at the largest sizes the library accepts.
 
-N = 112 is the largest basis a context takes (the Dyson kernel keeps its share
-of the N(N+1)/2 triangle in registers and the natural-occupation sweep keeps
-the N x N matrix in shared memory).  N = 80 and N = 112 run the two widest
-register layouts of the Dyson kernel (9 and 16 triangle elements per thread),
-which the physical workloads (N <= 64) never reach.  Inputs are seeded; the
-expected values come from ``oracle/``.
+N = 128 (the H64 lattice in 6-31G) is the largest basis a context takes: the
+Dyson kernel keeps its share of the N(N+1)/2 triangle in registers and the
+natural-occupation sweep keeps the N x N matrix in shared memory.  N = 80, 112
+and 128 run the three widest register layouts of the Dyson kernel (9, 16 and
+17 triangle elements per thread), which the N <= 64 workloads never reach.
+Inputs are seeded; the expected values come from ``oracle/``.
 
 The per-frequency matrices are complex symmetric with a positive-definite
 imaginary part (omega_n S - Im Sigma, Im Sigma <= 0), the class for which the
@@ -26,7 +26,7 @@ from oracle.occupations import natural_occupations
 
 pytestmark = pytest.mark.gpu
 
-N_MAX = 112
+N_MAX = 128
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +72,7 @@ def sigma_iw(n, n_iw, seed, scale=0.005):
     return x + np.swapaxes(x, 1, 2)
 
 
-@pytest.mark.parametrize("n", [80, N_MAX])
+@pytest.mark.parametrize("n", [80, 112, N_MAX])
 def test_tail_dyson_density_energy_at_largest_bases(g, n):
     beta, n_tau, n_iw, mu = 10.0, 9, 64, -0.05
     S, F, h, sig1, sig2 = one_body(n, seed=500 + n)
@@ -99,24 +99,22 @@ def test_tail_dyson_density_energy_at_largest_bases(g, n):
     assert abs(e2 - e2_ref) <= 1e-11 * max(1.0, abs(e2_ref))
 
 
-@pytest.fixture(scope="module")
-def v_max():
-    return gi.random_eri(N_MAX, seed=5) * 0.1
-
-
-def test_sigma_fp64_and_fock_at_largest_basis(g, v_max):
-    """One grid point of Eq. Sigma (FP64 path: two 64-wide tiles with a
-    48-wide ragged one in every stage) and Eq. FockMatrix at N = 112."""
-    n, n_tau, k = N_MAX, 9, 3
+@pytest.mark.parametrize("n", [112, N_MAX])
+def test_sigma_fp64_and_fock_at_largest_basis(g, n):
+    """One grid point of Eq. Sigma on the FP64 path and Eq. FockMatrix at
+    N = 128 (two full 64-wide GEMM tiles in every stage), and at N = 112 (a
+    48-wide ragged tile)."""
+    n_tau, k = 9, 3
+    v = gi.random_eri(n, seed=5) * 0.1
     G = gi.random_symmetric_g(n, n_tau, seed=6)
-    ref = osg.sigma_factored(G[k], -G[n_tau - 1 - k], v_max)
+    ref = osg.sigma_factored(G[k], -G[n_tau - 1 - k], v)
     S, F, h, _, _ = one_body(n, seed=7)
     rng = np.random.default_rng(8)
     A = rng.uniform(-1.0, 1.0, size=(n, n))
     P = 0.1 * (A @ A.T) / n
-    F_ref = oracle_fock(h, v_max, P)
+    F_ref = oracle_fock(h, v, P)
     with g.Context(n, n_tau, 8, 10.0) as ctx:
-        g.gf2_set_integrals(ctx.handle, dev(v_max))
+        g.gf2_set_integrals(ctx.handle, dev(v))
         out = torch.zeros(1, n, n, dtype=torch.float64, device="cuda")
         g.gf2_sigma_tau_points(ctx.handle, dev(G), k, 1, out, g.GF2_PREC_FP64)
         Fd = torch.zeros(n, n, dtype=torch.float64, device="cuda")
@@ -130,7 +128,7 @@ def test_sigma_fp64_and_fock_at_largest_basis(g, v_max):
         g.gf2_sigma_tau_points(ctx.handle, dev(G), k, 1, out2, g.GF2_PREC_FP64)
         again = host(out2)[0]
     assert np.abs(again - got).max() <= 1e-13 * np.abs(got).max()
-    # FP64 sums of up to N^3 = 1.4e6 products per entry in another order than numpy's
+    # FP64 sums of up to N^3 = 2.1e6 products per entry in another order than numpy's
     assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
     assert np.abs(got_F - F_ref).max() <= 1e-12 * max(1.0, np.abs(F_ref).max())
 

@@ -64,7 +64,7 @@ def test_noalloc_energy_rejects_sizes_beyond_its_scratch():
     x = torch.zeros(4, dtype=torch.float64, device="cuda")
     p = ctypes.c_void_p(x.data_ptr())
     e1, e2 = ctypes.c_double(), ctypes.c_double()
-    # n_iw above 65536 and N above 112 are refused before any launch (GF2_ERR_UNSUPPORTED = 7)
+    # n_iw above 65536 and N above 128 are refused before any launch (GF2_ERR_UNSUPPORTED = 7)
     assert f(2, 65537, 10.0, p, p, p, p, p, p, None, ctypes.byref(e1), ctypes.byref(e2), None) == 7
-    assert f(113, 8, 10.0, p, p, p, p, p, p, None, ctypes.byref(e1), ctypes.byref(e2), None) == 7
+    assert f(129, 8, 10.0, p, p, p, p, p, p, None, ctypes.byref(e1), ctypes.byref(e2), None) == 7
     assert f(2, 8, 10.0, None, p, p, p, p, p, None, ctypes.byref(e1), ctypes.byref(e2), None) == 1

@@ -175,7 +175,10 @@ gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
                          double *d_P, int *n_eval);
 
 /* Eq. FockMatrix: F_ij = h_ij + sum_kl P_kl (v_ijlk - v_iklj / 2), with the
- * integrals given to gf2_set_integrals. */
+ * integrals given to gf2_set_integrals (no index symmetry of v is assumed).
+ * d_h, d_P [N][N] in, d_F [N][N] out.  d_F may be d_h (F replaces h in
+ * place) but must not be d_P (GF2_ERR_ARG).  The sums are accumulated with
+ * FP64 atomics, so their rounding order varies from call to call. */
 gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_P, double *d_F);
 
 /* Galitskii-Migdal energy (the paper reports energies but prints no formula):

@@ -60,8 +60,10 @@ __global__ void moments_kernel(int N2, double mu, const double *basis, double *m
 constexpr int kDysonThreads = 512;
 constexpr int kDysonMaxPerThread = (GF2_MAX_N * (GF2_MAX_N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
 
-template <int PER>
-__global__ void __launch_bounds__(kDysonThreads, 1)
+// MINB = 2 (at most 64 registers) for the narrow layouts, so that two CTAs
+// share an SM and one's barrier waits overlap the other's sweep.
+template <int PER, int MINB>
+__global__ void __launch_bounds__(kDysonThreads, MINB)
     dyson_kernel(int N, double beta, double mu, const double *__restrict__ S, const double *__restrict__ F,
                  const double2 *__restrict__ Sig, double2 *__restrict__ G, int *flag) {
   __shared__ double2 v[GF2_MAX_N];  // pivot column a_ik
@@ -195,21 +197,81 @@ __global__ void trace_kernel(int N, const double *P, const double *S, double *ou
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// F_ij = h_ij + sum_kl P_kl (v_ijlk - v_iklj / 2), with v_ijlk = v_lkij (real ERIs)
-__global__ void fock_kernel(int N, const double *__restrict__ h, const double *__restrict__ v,
-                            const double *__restrict__ P, double *__restrict__ F) {
-  const int i = blockIdx.x, j = threadIdx.x;
-  if (j >= N) return;
-  const long long N2 = (long long)N * N, N3 = N2 * N;
-  double acc = 0.0;
-  for (int k = 0; k < N; ++k)
-    for (int l = 0; l < N; ++l) {
-      const double p = P[k * N + l];
-      const double coul = v[(long long)l * N3 + (long long)k * N2 + (long long)i * N + j];   // v_lkij
-      const double exch = v[(long long)i * N3 + (long long)k * N2 + (long long)l * N + j];   // v_iklj
-      acc += p * (coul - 0.5 * exch);
+// Eq. FockMatrix, F = h + J - K/2 with J_ij = sum_kl P_kl v_ijlk and
+// K_ij = sum_kl P_kl v_iklj, in one pass over v (HBM-bound: N^4 doubles read
+// once).  Element v[a,b,c,d] adds v P[d,c] to J[a,b] and P[b,c] v to K[a,d].
+// CTA (a, block of b rows): warp w takes rows c = w, w + 8, ... of v[a,b],
+// lane l the columns d = l + 32 q (q < 4, N <= 128), four rows in flight per
+// warp.  P^T sits in shared memory, so the column read P[d,c] is conflict-free.
+// F holds h on entry (copied before the launch); each CTA adds its J entries
+// and its partial K row by FP64 atomics.
+constexpr int kFockThreads = 256, kFockWarps = kFockThreads / 32, kFockQ = 4, kFockUnroll = 4;
+static_assert(GF2_MAX_N <= 32 * kFockQ, "fock_kernel covers N <= 32 kFockQ columns");
+
+__global__ void __launch_bounds__(kFockThreads)
+    fock_kernel(int N, int b_per_cta, const double *__restrict__ v, const double *__restrict__ P,
+                double *__restrict__ F) {
+  extern __shared__ double fock_sm[];
+  double *Pt = fock_sm;                          // [N][N]: Pt[c N + d] = P[d N + c]
+  double *jred = Pt + N * N;                     // [warps][b_per_cta]
+  double *kred = jred + kFockWarps * b_per_cta;  // [warps][N]
+  const int a = blockIdx.x, b0 = blockIdx.y * b_per_cta, b1 = min(N, b0 + b_per_cta);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int e = threadIdx.x; e < N * N; e += kFockThreads) {
+    const int d = e / N, c = e - d * N;
+    Pt[c * N + d] = P[e];
+  }
+  __syncthreads();
+  double kacc[kFockQ] = {};
+  for (int b = b0; b < b1; ++b) {
+    const double *vb = v + ((size_t)a * N + b) * N * N;  // v[a, b, :, :]
+    double jpart = 0.0;
+    for (int c0 = warp; c0 < N; c0 += kFockWarps * kFockUnroll) {
+      double x[kFockUnroll][kFockQ];
+#pragma unroll
+      for (int u = 0; u < kFockUnroll; ++u) {
+        const int c = c0 + u * kFockWarps;
+#pragma unroll
+        for (int q = 0; q < kFockQ; ++q) {
+          const int d = lane + 32 * q;
+          x[u][q] = (c < N && d < N) ? vb[(size_t)c * N + d] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kFockUnroll; ++u) {
+        const int c = c0 + u * kFockWarps;
+        if (c >= N) break;
+        const double pbc = Pt[c * N + b];  // P[b, c]
+#pragma unroll
+        for (int q = 0; q < kFockQ; ++q) {
+          const int d = lane + 32 * q;
+          if (d < N) {
+            jpart = fma(x[u][q], Pt[c * N + d], jpart);  // v[a,b,c,d] P[d,c]
+            kacc[q] = fma(pbc, x[u][q], kacc[q]);        // P[b,c] v[a,b,c,d]
+          }
+        }
+      }
     }
-  F[i * N + j] = h[i * N + j] + acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) jpart += __shfl_xor_sync(0xffffffffu, jpart, off);
+    if (lane == 0) jred[warp * b_per_cta + (b - b0)] = jpart;
+  }
+#pragma unroll
+  for (int q = 0; q < kFockQ; ++q) {
+    const int d = lane + 32 * q;
+    if (d < N) kred[warp * N + d] = kacc[q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += kFockThreads) {
+    double k = 0.0;
+    for (int w = 0; w < kFockWarps; ++w) k += kred[w * N + t];
+    atomicAdd(&F[(size_t)a * N + t], -0.5 * k);
+  }
+  for (int t = threadIdx.x; t < b1 - b0; t += kFockThreads) {
+    double j = 0.0;
+    for (int w = 0; w < kFockWarps; ++w) j += jred[w * b_per_cta + t];
+    atomicAdd(&F[(size_t)a * N + b0 + t], j);
+  }
 }
 
 // partial[n] = sum_ij Re(G_ij Sigma_ji) at frequency n (32x32 tiles through smem)
@@ -348,13 +410,13 @@ gf2_status launch_dyson(gf2_ctx *ctx, double mu, const double *S, const double *
   const double2 *sg = reinterpret_cast<const double2 *>(Sig);
   double2 *gg = reinterpret_cast<double2 *>(G);
   cudaStream_t st = ctx->stream;
-  if (per <= 1) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else if (per <= 2) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else if (per <= 4) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<4><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else if (per <= 5) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<5><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else if (per <= 9) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<9><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else if (per <= 16) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<16><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
-  else GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<kDysonMaxPerThread><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  if (per <= 1) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<1, 2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 2) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<2, 2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 4) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<4, 2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 5) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<5, 2><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 9) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<9, 1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else if (per <= 16) GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<16, 1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
+  else GF2_PROF(ctx, GF2_K_DYSON, (dyson_kernel<kDysonMaxPerThread, 1><<<nb, kDysonThreads, 0, st>>>(N, ctx->beta, mu, S, F, sg, gg, ctx->d_err)));
   GF2_CK_LAUNCH(ctx, "dyson_kernel");
   return GF2_OK;
 }
@@ -591,8 +653,18 @@ extern "C" gf2_status gf2_fock(gf2_ctx *ctx, const double *d_h, const double *d_
   if (!ctx) return GF2_ERR_ARG;
   if (!d_h || !d_P || !d_F) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: NULL pointer");
   if (!ctx->have_integrals) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: gf2_set_integrals not called");
+  if (d_F == d_P) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fock: d_F must not alias d_P");
+  const int N = ctx->N;
+  // about four CTAs per SM: N rows a times ceil(N / b_per_cta) blocks of b
+  const int want = std::min(N, std::max(1, (4 * ctx->num_sms + N - 1) / N));
+  const int b_per_cta = (N + want - 1) / want;
+  const dim3 grid(N, (N + b_per_cta - 1) / b_per_cta);
+  const size_t smem = sizeof(double) * ((size_t)N * N + (size_t)kFockWarps * b_per_cta + (size_t)kFockWarps * N);
+  GF2_CK(ctx, cudaFuncSetAttribute(fock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (d_F != d_h)
+    GF2_CK(ctx, cudaMemcpyAsync(d_F, d_h, sizeof(double) * N * N, cudaMemcpyDeviceToDevice, ctx->stream));
   GF2_PROF(ctx, GF2_K_FOCK,
-           (fock_kernel<<<ctx->N, ((ctx->N + 31) / 32) * 32, 0, ctx->stream>>>(ctx->N, d_h, ctx->d_v, d_P, d_F)));
+           (fock_kernel<<<grid, kFockThreads, smem, ctx->stream>>>(N, b_per_cta, ctx->d_v, d_P, d_F)));
   GF2_CK_LAUNCH(ctx, "fock_kernel");
   return GF2_OK;
 }

@@ -170,6 +170,32 @@ def test_mu_search_and_fock_match_oracle(library, h4):
     assert np.abs(got_F - oracle_fock(s.h, s.eri, P_ref)).max() < 1e-12
 
 
+@pytest.mark.parametrize("n", [4, 5, 33, 64])
+def test_fock_matches_oracle_without_index_symmetry(library, n):
+    """Eq. FockMatrix on a v and a P with no index symmetry (the build reads
+    v_ijlk and v_iklj as given); F in place of h; F aliasing P is refused."""
+    g = library
+    rng = np.random.default_rng(40 + n)
+    v = rng.normal(size=(n, n, n, n))
+    P = rng.normal(size=(n, n))
+    h = rng.normal(size=(n, n))
+    ref = oracle_fock(h, v, P)
+    with g.Context(n, 9, 8, 10.0) as ctx:
+        g.gf2_set_integrals(ctx.handle, dev(v))
+        F = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+        g.gf2_fock(ctx.handle, dev(h), dev(P), F)
+        got = host(F)
+        hd = dev(h)
+        g.gf2_fock(ctx.handle, hd, dev(P), hd)
+        in_place = host(hd)
+        Pd = dev(P)
+        with pytest.raises(g.GF2Error):
+            g.gf2_fock(ctx.handle, dev(h), Pd, Pd)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    assert np.abs(in_place - ref).max() <= 1e-12 * scale
+
+
 def test_mu_search_coarse_stage_matches_oracle(library, h4):
     """n_iw = 2048 switches on the coarse (n_iw/8 frequency) stage of the GPU
     search; with a correlated Sigma the converged count and P must still match

@@ -26,8 +26,8 @@
  *  - The context owns its workspace (intermediates, split copies of the
  *    integrals, grid tables) and allocates it at gf2_create /
  *    gf2_set_integrals.  All work is stream-ordered on the context stream;
- *    calls that return host scalars (gf2_mu_search, gf2_energy) synchronize
- *    that stream.
+ *    calls that return host scalars or check a device error word synchronize
+ *    that stream (each says so below).
  *  - Every call returns a gf2_status.  Invalid sizes or NULL pointers give
  *    GF2_ERR_ARG before any launch; a CUDA failure gives GF2_ERR_CUDA; device
  *    loops that give up after their iteration limit report GF2_ERR_TIMEOUT.
@@ -108,7 +108,11 @@ gf2_status gf2_set_overlap(gf2_ctx *ctx, const double *d_S);
 /* Eq. Sigma (the paper's second-order self-energy):
  *   Sigma_ij(tau) = - sum_klmnpq G_kl(tau) G_mn(tau) G_pq(-tau) v_imqk (2 v_lpnj - v_nplj)
  * with G(-tau_k) = -G(tau_{M-k}).  d_G_tau [n_tau][N][N] in, d_Sigma_tau
- * [n_tau][N][N] out.  Requires gf2_set_integrals first. */
+ * [n_tau][N][N] out.  Requires gf2_set_integrals first.  prec is a gf2_prec;
+ * the split precisions need N <= 64 (else GF2_ERR_UNSUPPORTED, the context
+ * stays usable) and synchronize the context stream to read the pipeline's
+ * error word (GF2_ERR_TIMEOUT if a bounded wait gave up); FP64 is
+ * stream-ordered. */
 gf2_status gf2_sigma_tau(gf2_ctx *ctx, const double *d_G_tau, double *d_Sigma_tau, int prec);
 
 /* The same for the `count` grid points k0 .. k0+count-1 only: d_G_tau is the

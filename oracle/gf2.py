@@ -11,7 +11,8 @@
 Optional damping (the supplement damps P in the inner loop and Sigma(tau) in
 the outer loop without stating amounts): P <- a_P P_new + (1-a_P) P_old and
 Sigma <- a_S Sigma_new + (1-a_S) Sigma_old, both 1 (no damping) by default.
-The inner loop extrapolates F by Pulay's DIIS (see ``inner_loop``).
+The inner loop takes damped steps far from its fixed point and Pulay (DIIS)
+extrapolation near it (see ``inner_loop``).
 """
 
 from dataclasses import dataclass, field
@@ -49,17 +50,22 @@ def _diis_coefficients(gram):
     return np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
 
 
-def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-8, max_iter=200,
-               p_damping=1.0, diis=8):
+def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-8, max_iter=300,
+               p_damping=1.0, diis=8, mix=0.5, diis_from=1e-3):
     """Steps 2.a-2.b: alternate the mu search and the Fock rebuild to self-consistency.
 
     Converged when the Fock residual R = F(P(F)) - F has Frobenius norm below
     ``tol`` (the mu search stops anywhere within 1e-10 electrons, which leaves
-    a noise floor near 1e-9 in R).  With ``diis`` > 0 the next F is the Pulay
-    extrapolation of the
-    last ``diis`` rebuilt matrices (the plain fixed-point map is unstable for
-    some lattices at finite temperature); G, P and mu are then re-evaluated at
-    the converged F.
+    a noise floor near 1e-9 in R).  The schedule of the next F:
+      * far from the fixed point, |R| > ``diis_from`` (or ``diis`` <= 0): the
+        damped step F + ``mix`` R (``mix`` = 1 is the plain map F <- F(P(F)));
+      * closer in: the Pulay (DIIS) extrapolation of the last ``diis``
+        rebuilt matrices, the history restarting whenever a damped step is
+        taken.
+    (The plain map is unstable for some lattices at finite temperature, and
+    from the HF state of a correlated lattice the fixed point can sit 20 mEh
+    away in mu, where DIIS alone wanders.)  G, P and mu are then re-evaluated
+    at the converged F.
     """
     S, h, v = system.S, system.h, system.eri
     P_old = None
@@ -71,20 +77,22 @@ def inner_loop(system, F, Sigma_iw, sig1, sig2, beta, n_iw, tol=1e-8, max_iter=2
         P_old = P
         F_out = fock(h, v, P)
         R = F_out - F
-        if np.sqrt(np.sum(R * R)) < tol:
+        r_norm = np.sqrt(np.sum(R * R))
+        if r_norm < tol:
             F = F_out
             mu, G, P, _ = dy.mu_search(S, F, Sigma_iw, sig1, sig2, system.n_elec, beta, n_iw)
             return F, mu, G, P
-        if diis > 0:
-            hist_F.append(F_out)
-            hist_R.append(R)
-            hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
-            if len(hist_F) > 1:
-                gram = np.array([[np.sum(a * b) for b in hist_R] for a in hist_R])
-                c = _diis_coefficients(gram)
-                F = sum(ci * fi for ci, fi in zip(c, hist_F))
-            else:
-                F = F_out
+        if r_norm > diis_from or diis <= 0:
+            hist_F, hist_R = [], []
+            F = F + mix * R
+            continue
+        hist_F.append(F_out)
+        hist_R.append(R)
+        hist_F, hist_R = hist_F[-diis:], hist_R[-diis:]
+        if len(hist_F) > 1:
+            gram = np.array([[np.sum(a * b) for b in hist_R] for a in hist_R])
+            c = _diis_coefficients(gram)
+            F = sum(ci * fi for ci, fi in zip(c, hist_F))
         else:
             F = F_out
     raise RuntimeError("inner loop did not converge")
@@ -107,11 +115,11 @@ def self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn=None):
 
 
 def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damping=1.0,
-        p_damping=1.0, inner_tol=1e-8, sigma_fn=None, callback=None, diis=8):
+        p_damping=1.0, inner_tol=1e-8, sigma_fn=None, callback=None, diis=8, mix=0.5, diis_from=1e-3):
     """Full GF2; returns the final GF2State (energies[] holds (E, E1, E2) per iteration)."""
     n = system.nbf
     F, mu, G, P = inner_loop(system, F_start, None, None, None, beta, n_iw, inner_tol,
-                             p_damping=p_damping, diis=diis)
+                             p_damping=p_damping, diis=diis, mix=mix, diis_from=diis_from)
     state = GF2State(F=F, mu=mu, P=P, G_iw=G, sig1=np.zeros((n, n)), sig2=np.zeros((n, n)))
     state.energies.append(energy(system, state, beta))
     for _ in range(max_outer):
@@ -123,7 +131,7 @@ def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damp
         state.sig1, state.sig2 = sigma_expansion(Sig_tau, beta)
         state.F, state.mu, state.G_iw, state.P = inner_loop(
             system, state.F, state.Sigma_iw, state.sig1, state.sig2, beta, n_iw, inner_tol,
-            p_damping=p_damping, diis=diis)
+            p_damping=p_damping, diis=diis, mix=mix, diis_from=diis_from)
         state.energies.append(energy(system, state, beta))
         if callback is not None:
             callback(state)

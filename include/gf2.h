@@ -258,13 +258,16 @@ gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, dou
                                  int prec);
 
 /* Allocation-free Galitskii-Migdal energy (no counterpart in the paper).
- * Same inputs, outputs and arithmetic as gf2_energy, but without a context
- * and without allocating: for callers that cannot call cudaMalloc -- code
- * running while a CUDA graph is captured, inside host callbacks, or in hosts
- * that give the library a fixed memory budget and forbid the device
- * allocator.  Its scratch (per-frequency partial sums, S^-1, the results) is
- * a fixed __device__ array of 65536 + 128*128 + 8 doubles (about 655 KB) that
- * every device loading the library keeps until the process exits.
+ * The same inputs and outputs as gf2_energy, and the same result to rounding
+ * (S^-1 comes from its own Gauss-Jordan sweep), but without a context and
+ * without allocating device memory.  It is meant for callers that cannot call
+ * cudaMalloc: a host program that gives the library a fixed device-memory
+ * budget and forbids the device allocator (an embedding whose own pool owns
+ * every byte of the GPU), or code that must not fail on an out-of-memory
+ * allocation in the middle of a run.  Its scratch (per-frequency partial sums,
+ * S^-1, the two results) is a fixed __device__ array of 65536 + 128*128 + 8
+ * doubles (about 655 KB) that every device loading the library keeps until
+ * the process exits.
  *   Limits: n_bf <= 128 and n_iw <= 65536, else GF2_ERR_UNSUPPORTED before any
  *   launch; NULL pointers or bad sizes give GF2_ERR_ARG; CUDA failures
  *   GF2_ERR_CUDA.  d_sig12 may be NULL (no tail term).
@@ -273,8 +276,8 @@ gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, dou
  *   capture.  Every call overwrites the shared array and fully rewrites what it
  *   reads, so consecutive calls are independent; calls that overlap on the GPU
  *   (other streams or threads at the same time) race on it.
- *   Runs on `stream` (a cudaStream_t; NULL = legacy default stream) and
- *   synchronizes it to return the two host scalars. */
+ *   Runs on `stream` (a cudaStream_t; NULL = legacy default stream), copies the
+ *   two results to the host and synchronizes that stream before returning. */
 gf2_status gf2_energy_noalloc(int n_bf, int n_iw, double beta, const double *d_h, const double *d_F,
                               const double *d_P, const double *d_S, const double *d_G_iw,
                               const double *d_Sigma_iw, const double *d_sig12, double *e_one_body,

@@ -310,6 +310,11 @@ __global__ void energy_partial_kernel(int N, const double2 *__restrict__ G, cons
   if (threadIdx.x == 0) partial[n] = red[0];
 }
 
+// Trigamma psi_1(x) for x > 0 by the standard method of Abramowitz & Stegun
+// (Handbook of Mathematical Functions, 6.4.6 and 6.4.12): the recurrence
+// psi_1(x) = psi_1(x + 1) + 1/x^2 raises the argument to x >= 20, where the
+// asymptotic series 1/x + 1/(2x^2) + sum_k B_2k / x^(2k+1) (Bernoulli numbers
+// B_2..B_10 = 1/6, -1/30, 1/42, -1/30, 5/66) is accurate to rounding.
 __device__ double trigamma(double x) {
   double acc = 0.0;
   while (x < 20.0) {
@@ -696,14 +701,14 @@ extern "C" gf2_status gf2_energy(gf2_ctx *ctx, const double *d_h, const double *
 // ---------------------------------------------------------------------------
 // Allocation-free variant of gf2_energy.
 //
-// For callers that must not allocate device memory at all -- code that runs
-// while a CUDA graph is being captured or replayed, inside a host callback,
-// or in an embedding that owns a fixed memory budget and forbids calls into
-// the device allocator -- this entry point needs no context and makes no
-// cudaMalloc/cudaFree (nor any allocating library call).  Its scratch (one
-// partial sum per frequency, S^-1 and the two results) lives in a file-scope
-// __device__ array of fixed size, present on every device that loads the
-// library until the process exits.
+// For callers that cannot allocate device memory -- a host that gives the
+// library a fixed memory budget and forbids the device allocator, or code that
+// must not meet an out-of-memory failure in the middle of a run -- this entry
+// point needs no context and makes no cudaMalloc/cudaFree (nor any allocating
+// library call).  Its scratch (one partial sum per frequency, S^-1 and the two
+// results) lives in a file-scope __device__ array of fixed size, present on
+// every device that loads the library until the process exits.  It copies the
+// two results to the host and synchronizes the caller's stream.
 // ---------------------------------------------------------------------------
 #include <mutex>
 

@@ -1,0 +1,101 @@
+"""The first GF2 self-energy step on the H32 2x4x4 lattice (2.0 bohr, 6-31G,
+N = 64, beta = 100) through the C-ABI, against the oracle's values for the
+same step stored in ``tests/golden/h32_631g_first_step_t*_w*.json`` (written
+by ``tests/golden/make_h32_631g_first_step.py``, which calls ``oracle/``
+only).  The step is the one the benchmark times: finite-temperature HF state
+(F_HF, mu from the Sigma = 0 search), tail moments, G(i w) -> G(tau),
+Sigma(tau) by Eq. Sigma, Sigma(tau) -> Sigma(i w), mu search at F_HF with that
+Sigma, Galitskii-Migdal energy with F = F_HF.
+
+Bounds: the FP64 path within 1e-8 Eh of the oracle energy and 1e-8 on every
+density element; the split tensor-core precisions within 1e-6 Eh and, on the
+benchmark's own grid (4097 time points, 8192 frequencies), 1e-6 on every
+density element.  The 257 / 512 fixture is a reduced grid of the same system:
+there each time point carries sixteen times the quadrature weight of
+Sigma(tau) -> Sigma(i w), and the split rounding errors of the points, which
+are independent, add up to sqrt(16) = 4 times the density error of the full
+grid, so the density bound there is 4e-6 (the measured FP16x3 error is 6e-7
+on the full grid and 3.4e-6 on the reduced one).
+"""
+
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import gf2_inputs as gi
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FIXTURES = sorted(glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_t*_w*.json")))
+BOUNDS = {0: (1e-8, 1e-8), 2: (1e-6, 1e-6), 3: (1e-6, 1e-6), 4: (1e-6, 1e-6)}
+
+
+@pytest.fixture(scope="module")
+def lattice():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1405_3273_gb300 as g
+    from paper_1405_3273_gb300 import build
+    if not os.path.exists(g.LIB_PATH):
+        build.build()
+    s = gi.build_system("h32_lattice_631g", spacing=2.0)
+    return g, s, gi.rhf(s)
+
+
+def first_step(g, s, r, n_tau, n_iw, beta, precs):
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    N = s.nbf
+    S, hc, F0 = f64(s.S), f64(s.h), f64(r.F)
+    out = {}
+    with g.Context(N, n_tau, n_iw, beta) as ctx:
+        h = ctx.handle
+        g.gf2_set_integrals(h, f64(s.eri))
+        g.gf2_set_overlap(h, S)
+        G0 = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+        P0 = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+        mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+        mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G0, P0)
+        e1_hf, _ = g.gf2_energy(h, hc, F0, P0, S, G0, torch.zeros_like(G0), None)
+        out["hf"] = (s.e_nuc + e1_hf, P0.cpu().numpy())
+        mom = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+        G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+        g.gf2_tail_moments(h, S, F0, mu_hf, None, mom)
+        g.gf2_fft_iw_to_tau(h, G0, mom, G_tau)
+        for prec in precs:
+            Sig = torch.empty_like(G_tau)
+            Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+            sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+            g.gf2_sigma_tau(h, G_tau, Sig, prec)
+            g.gf2_fft_tau_to_iw(h, Sig, Sig_iw, sig12)
+            G = torch.empty_like(G0)
+            P = torch.empty_like(P0)
+            g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, G, P)
+            e1, e2 = g.gf2_energy(h, hc, F0, P, S, G, Sig_iw, sig12)
+            out[prec] = (s.e_nuc + e1 + e2, P.cpu().numpy())
+    return out
+
+
+@pytest.mark.parametrize("path", FIXTURES, ids=[os.path.basename(p)[:-5] for p in FIXTURES])
+def test_first_step_matches_oracle(lattice, path):
+    g, s, r = lattice
+    ref = json.load(open(path))
+    assert ref["n_bf"] == s.nbf == 64
+    n_tau, n_iw, beta = ref["n_tau"], ref["n_iw"], ref["beta"]
+    P_ref = np.array(ref["P"])
+    got = first_step(g, s, r, n_tau, n_iw, beta, sorted(BOUNDS))
+    e_hf, P_hf = got["hf"]
+    assert abs(e_hf - ref["E_hf"]) < 1e-9
+    assert abs(np.trace(P_hf @ s.S) - s.n_elec) <= 1e-10
+    for prec, (e_tol, p_tol) in BOUNDS.items():
+        if prec != 0:
+            p_tol *= np.sqrt(4096.0 / (n_tau - 1))
+        E, P = got[prec]
+        dE, dP = abs(E - ref["E"]), np.abs(P - P_ref).max()
+        print(f"{os.path.basename(path)} prec {prec}: |dE| {dE:.2e} Eh, max|dP| {dP:.2e}")
+        assert dE <= e_tol, (prec, dE)
+        assert dP <= p_tol, (prec, dP)
+        assert abs(np.trace(P @ s.S) - s.n_elec) <= 1e-10

@@ -107,6 +107,24 @@ def test_split_sigma_n64_sampled_points(g, prec, rtol):
         assert rel <= rtol, k
 
 
+@pytest.mark.parametrize("prec,rtol", [(2, 3e-6), (3, 3e-6)])
+def test_split_sigma_without_pair_symmetry(g, prec, rtol):
+    """Integrals that lack the pair symmetry (im|qk) = (qk|im) make the library
+    compute every tile of the stage-2 intermediate (the symmetric run computes
+    half and mirrors them, which would be wrong here).  Sigma is then not
+    symmetric either, and the library returns its symmetric part."""
+    n, n_tau = 64, 9
+    G = gi.random_symmetric_g(n, n_tau, seed=41) * 0.3
+    rng = np.random.default_rng(42)
+    v = gi.random_eri(n, seed=43) + 0.05 * rng.normal(size=(n, n, n, n))
+    ref = osg.sigma_tau(G, v)
+    ref = 0.5 * (ref + np.swapaxes(ref, 1, 2))
+    got = _split_sigma(g, G, v, prec)
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"split Sigma without pair symmetry, prec={prec}: max rel error {rel:.3e}")
+    assert rel <= rtol
+
+
 @pytest.fixture(scope="module")
 def n64_every_point_case():
     n, n_tau, count = 64, 65, 37

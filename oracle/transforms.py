@@ -88,18 +88,20 @@ def _phase(n_idx, k_idx, M, sign):
     return np.exp(sign * 1j * np.pi * num / M)
 
 
-def iw_to_tau(X_iw, moments, beta, n_tau, chunk=512):
-    """[n_tau, N, N] real X(tau_k) from X(i w_n), n = 0..n_iw-1."""
+def iw_to_tau(X_iw, moments, beta, n_tau, chunk=512, taus=None):
+    """[n_tau, N, N] real X(tau_k) from X(i w_n), n = 0..n_iw-1 (or only the
+    grid indices listed in ``taus``, in that order)."""
     n_iw, n, _ = X_iw.shape
     M = n_tau - 1
+    ks_all = np.arange(n_tau) if taus is None else np.asarray(taus, dtype=np.int64)
     w = matsubara(beta, n_iw)
     R = (X_iw - tail_iw(moments, w)).reshape(n_iw, n * n)
-    out = np.empty((n_tau, n * n))
-    for k0 in range(0, n_tau, chunk):
-        ks = np.arange(k0, min(n_tau, k0 + chunk))
+    out = np.empty((len(ks_all), n * n))
+    for i0 in range(0, len(ks_all), chunk):
+        ks = ks_all[i0:i0 + chunk]
         E = _phase(np.arange(n_iw), ks, M, -1.0)
-        out[ks] = (2.0 / beta) * np.real(E @ R)
-    return out.reshape(n_tau, n, n) + tail_tau(moments, tau_grid(beta, n_tau), beta)
+        out[i0:i0 + len(ks)] = (2.0 / beta) * np.real(E @ R)
+    return out.reshape(len(ks_all), n, n) + tail_tau(moments, tau_grid(beta, n_tau)[ks_all], beta)
 
 
 def _monomial_moments(theta):

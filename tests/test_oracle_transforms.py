@@ -128,3 +128,16 @@ def test_pole_tail_has_the_moment_expansion_and_its_tau_image():
         unit[:, 0, 0] = np.linalg.solve(L, c)
         got = ot.tail_tau(unit, taus, beta)[:, 0, 0]
         assert np.abs(got - fd[r]).max() < 2e-5
+
+
+def test_iw_to_tau_on_selected_points_equals_the_full_grid_rows():
+    """The subset option (used to time the oracle on a sample of time points)
+    returns exactly the rows of the full transform."""
+    rng = np.random.default_rng(11)
+    n, beta, n_tau, n_iw = 3, 20.0, 33, 48
+    X = rng.normal(size=(n_iw, n, n)) + 1j * rng.normal(size=(n_iw, n, n))
+    mom = rng.normal(size=(4, n, n))
+    full = ot.iw_to_tau(X, mom, beta, n_tau)
+    taus = [5, 0, 32, 17]
+    sub = ot.iw_to_tau(X, mom, beta, n_tau, taus=taus)
+    assert np.abs(sub - full[taus]).max() <= 1e-14 * np.abs(full).max()

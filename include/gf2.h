@@ -92,7 +92,8 @@ const char *gf2_last_error(const gf2_ctx *ctx);
 /* Copy the two-electron integrals v [N^4] into the context and build the
  * exchange combination W_lpnj = 2 v_lpnj - v_nplj of Eq. Sigma plus its BF16
  * and FP16 split copies for the tensor-core path (for N <= 32 as floor(64/N)
- * diagonal blocks, so that several time points share one 64-wide tile). */
+ * diagonal blocks, so that several time points share one 64-wide tile; for
+ * N > 64 the 128-wide copies are built by the first split-precision call). */
 gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v);
 
 /* Give the context the overlap S [N][N] (symmetric positive definite).  The
@@ -109,10 +110,14 @@ gf2_status gf2_set_overlap(gf2_ctx *ctx, const double *d_S);
  *   Sigma_ij(tau) = - sum_klmnpq G_kl(tau) G_mn(tau) G_pq(-tau) v_imqk (2 v_lpnj - v_nplj)
  * with G(-tau_k) = -G(tau_{M-k}).  d_G_tau [n_tau][N][N] in, d_Sigma_tau
  * [n_tau][N][N] out.  Requires gf2_set_integrals first.  prec is a gf2_prec;
- * the split precisions need N <= 64 (else GF2_ERR_UNSUPPORTED, the context
- * stays usable) and synchronize the context stream to read the pipeline's
+ * the split precisions run on 64-wide tiles for N <= 64 and on 128-wide tiles
+ * for 64 < N <= 128 (whose term planes, about 6.4 GB, and FP32 intermediates,
+ * up to 2 x 16 GB for chunks of 16 time points, are allocated by the first
+ * split call), and synchronize the context stream to read the pipeline's
  * error word (GF2_ERR_TIMEOUT if a bounded wait gave up); FP64 is
- * stream-ordered. */
+ * stream-ordered.  When v has the pair symmetry (ij|kl) = (kl|ij) (checked at
+ * gf2_set_integrals, to 1e-12 relative) the 64-wide path computes half of the
+ * stage-2 intermediate and mirrors it. */
 gf2_status gf2_sigma_tau(gf2_ctx *ctx, const double *d_G_tau, double *d_Sigma_tau, int prec);
 
 /* The same for the `count` grid points k0 .. k0+count-1 only: d_G_tau is the

@@ -53,6 +53,8 @@ struct gf2_ctx {
   int e_v16 = 0, e_w16 = 0;
   double vmax16 = 0.0;          // largest |v| after its FP16 scale
   int split_terms = 0;
+  bool tc_pair_sym = false;     // v[i][m][q][k] = v[q][k][i][m] to rounding: the sandwich computes half the tiles
+  bool tc_planes_stale = false; // N > 64: the 128-wide planes are built by the first split-precision call
 
   // grid tables (built at create)
   double2 *d_twiddle = nullptr;   // e^{-2 pi i k / M}, k < M/2
@@ -70,6 +72,7 @@ struct gf2_ctx {
 
   // tensor-core Sigma workspace (host-side state owning device buffers)
   void *d_tc_ws = nullptr;
+  void *d_tc128_ws = nullptr;     // the same for the 128-wide tile pipeline
   size_t tc_ws_bytes = 0;
   int tc_chunk = 0;
   int tc_chunk_max = 32;           // slots per split-pipeline launch (even, 2..32; the batch tuner sets it)
@@ -144,7 +147,12 @@ gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G_tau, int k0, int count
 gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out,
                         int prec);
 gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx);
+gf2_status gf2_tc_build_planes(gf2_ctx *ctx, int P);
 void gf2_tc_release(gf2_ctx *ctx);
+// 128-wide tile pipeline (64 < N <= 128)
+gf2_status gf2_tc128_workspace(gf2_ctx *ctx);
+gf2_status gf2_tc128_run(gf2_ctx *ctx, const double *d_G, int k0, int count, double *d_out, int prec);
+void gf2_tc128_release(gf2_ctx *ctx);
 gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int count, double **d_Gorth);
 gf2_status gf2_orth_transform_v(gf2_ctx *ctx, double *d_vorth);
 gf2_status gf2_symmetrize(gf2_ctx *ctx, double *d_X, int count);

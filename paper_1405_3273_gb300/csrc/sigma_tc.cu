@@ -59,17 +59,16 @@
 #include <cudaTypedefs.h>
 
 #include "gf2_internal.cuh"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
 
 constexpr int NP = 64;
-constexpr int TMAX = 3;
 constexpr uint32_t TILE128 = 128 * NP * 2;  // 16 KB: 128 rows x 64 bf16
 constexpr uint32_t TILE64 = 64 * NP * 2;    //  8 KB: 64 rows x 64 bf16
 constexpr uint32_t kIdescKK = tc::idesc_bf16(128, 64, 0, 0);
 constexpr uint32_t kIdescMK = tc::idesc_bf16(128, 64, 1, 0);
-constexpr int kErrTimeout = 1;
 // 64-wide K steps per FP32 group in stage 4 (four doubled the BF16x6 error)
 template <int T>
 constexpr int contract_group() { return 2; }
@@ -79,184 +78,11 @@ constexpr int contract_stages_f() { return T == 2 ? 5 : 4; }
 template <int T>
 constexpr int contract_stages_w() { return 4; }
 
-// product list (a, b) with a + b < T, smallest terms first
-template <int T>
-struct Products;
-template <>
-struct Products<2> {
-  static constexpr int n = 3;
-  __device__ static int a(int k) { return k == 0 ? 1 : 0; }
-  __device__ static int b(int k) { return k == 1 ? 1 : 0; }
-};
-template <>
-struct Products<3> {
-  static constexpr int n = 6;
-  __device__ static int a(int k) { const int t[6] = {2, 1, 0, 1, 0, 0}; return t[k]; }
-  __device__ static int b(int k) { const int t[6] = {0, 1, 2, 0, 1, 0}; return t[k]; }
-};
-
-// rounding of two FP32 values to a packed pair of 16-bit terms; `back` gets the
-// rounded values in FP32, so the caller can form the next residual
-template <int F>
-__device__ __forceinline__ uint32_t pack2(float a, float b, float2 &back) {
-  if constexpr (F == 0) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
-    back = __bfloat1622float2(p);
-    return *reinterpret_cast<const uint32_t *>(&p);
-  } else {
-    const __half2 p = __floats2half2_rn(a, b);
-    back = __half22float2(p);
-    return *reinterpret_cast<const uint32_t *>(&p);
-  }
-}
-
-// instruction descriptor of a kind::f16 MMA with BF16 (F = 0) or FP16 (F = 1) operands
-__host__ __device__ constexpr uint32_t idesc_fmt(int F, int M, int N, int a_mn_major, int b_mn_major) {
-  return F == 0 ? tc::idesc_bf16(M, N, a_mn_major, b_mn_major) : tc::idesc_f16(M, N, a_mn_major, b_mn_major);
-}
-
-// exponent e with 2^e * amax in [2^13, 2^14) (0 for an all-zero operand)
-__host__ __device__ inline int fp16_exponent(double amax) {
-  if (!(amax > 0.0)) return 0;
-  int E;
-  frexp(amax, &E);  // amax = f 2^E, f in [0.5, 1)
-  return 14 - E;
-}
-
-// FP16 scale exponents per time point of a chunk, [kExpSets][C] ints:
-// eg (G(tau)^T), egb (Gbar(tau)), r1 (T1 operand), max|T2| and max|T3| (float bits)
-enum { kExpG = 0, kExpGbar = 1, kExpT1 = 2, kMaxT2 = 3, kMaxT3 = 4, kExpSets = 5 };
-
-__device__ __forceinline__ float exp2_scale(int e) { return ldexpf(1.0f, e); }
-
-// scale that brings the largest |value| of a stored T2 or T3 (float bits) into [2^13, 2^14)
-__device__ __forceinline__ int fp16_exponent_bits(int bits) { return fp16_exponent((double)__int_as_float(bits)); }
-
-// largest |x| of a warp into slot[0] (nonnegative floats order like their bits)
-__device__ __forceinline__ void warp_absmax_to(int *slot, float m) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_int(m));
-}
-
-__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
-  return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
-__device__ __forceinline__ void raise_abort(volatile int *abort, int *err) {
-  *abort = 1;
-  atomicExch(err, kErrTimeout);
-}
-
-// eight consecutive fp32 values (times `scale`, FP16 only) -> T 16-bit terms,
-// 16 bytes per term at dst + t * plane
-template <int T, int F>
-__device__ __forceinline__ void split8_store(const float *v, uint8_t *dst, uint32_t plane, float scale) {
-  float x[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) x[e] = F == 0 ? v[e] : v[e] * scale;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    uint32_t w[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float2 f;
-      w[e] = pack2<F>(x[2 * e], x[2 * e + 1], f);
-      x[2 * e] -= f.x;
-      x[2 * e + 1] -= f.y;
-    }
-    *reinterpret_cast<uint4 *>(dst + t * plane) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-// Split one row of 64 fp32 values (a TMEM lane of an A operand, times
-// `scale` for FP16) into T 16-bit terms and write term t as 32 packed columns
-// at column taddr + 32 t.
-template <int T, int F>
-__device__ __forceinline__ void split_row_to_tmem(float *x, uint32_t taddr, float scale) {
-  if constexpr (F != 0) {
-#pragma unroll
-    for (int c = 0; c < 64; ++c) x[c] *= scale;
-  }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    uint32_t w[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      float2 f;
-      w[c] = pack2<F>(x[2 * c], x[2 * c + 1], f);
-      x[2 * c] -= f.x;
-      x[2 * c + 1] -= f.y;
-    }
-    tc::tmem_st_32x32b_x32(taddr + 32 * t, w);
-  }
-}
-
 constexpr uint32_t kF32Tile = 128 * NP * 4;  // one FP32 tile of 128 x 64 values (32 KB)
 
 // ---------------------------------------------------------------------------
 // splitting of the FP64 inputs
 // ---------------------------------------------------------------------------
-// x (already scaled) -> TMAX 16-bit terms of format F, as raw bits
-template <int F>
-__device__ __forceinline__ void split_f64(double x, uint16_t *p) {
-  double r = x;
-#pragma unroll
-  for (int t = 0; t < TMAX; ++t) {
-    if constexpr (F == 0) {
-      const __nv_bfloat16 h = __double2bfloat16(r);
-      p[t] = *reinterpret_cast<const uint16_t *>(&h);
-      r -= (double)__bfloat162float(h);
-    } else {
-      const __half h = __double2half(r);
-      p[t] = *reinterpret_cast<const uint16_t *>(&h);
-      r -= (double)__half2float(h);
-    }
-  }
-}
-
-// Vs[t][i][q][m][k] = split_t (2^e v[i][m][q][k]), block-diagonal with B
-// blocks of N (zero outside them)
-template <int F>
-__global__ void split_v_kernel(int N, int B, const double *__restrict__ v, int e, uint16_t *__restrict__ Vs) {
-  const size_t plane = (size_t)NP * NP * NP * NP;
-  const double sc = ldexp(1.0, e);
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = idx % NP, m = (idx / NP) % NP, q = (idx / (NP * NP)) % NP, i = idx / (NP * NP * NP);
-    const int b = i / N, o = b * N;
-    double x = 0.0;
-    if (b < B && m / N == b && q / N == b && k / N == b)
-      x = v[(((size_t)(i - o) * N + (m - o)) * N + (q - o)) * N + (k - o)] * sc;
-    uint16_t p[TMAX];
-    split_f64<F>(x, p);
-    for (int t = 0; t < TMAX; ++t) Vs[t * plane + idx] = p[t];
-  }
-}
-
-// Ws[t][j][l][n][p] = split_t (2^e W[l][p][n][j]),  W_lpnj = 2 v_lpnj - v_nplj,
-// block-diagonal with B blocks of N
-template <int F>
-__global__ void split_w_kernel(int N, int B, const double *__restrict__ v, int e, uint16_t *__restrict__ Ws) {
-  const size_t plane = (size_t)NP * NP * NP * NP;
-  const double sc = ldexp(1.0, e);
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < plane;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int p = idx % NP, n = (idx / NP) % NP, l = (idx / (NP * NP)) % NP, j = idx / (NP * NP * NP);
-    const int bk = j / N, o = bk * N;
-    double x = 0.0;
-    if (bk < B && l / N == bk && n / N == bk && p / N == bk) {
-      const int jj = j - o, ll = l - o, nn = n - o, pp = p - o;
-      const double a = v[(((size_t)ll * N + pp) * N + nn) * N + jj];
-      const double b = v[(((size_t)nn * N + pp) * N + ll) * N + jj];
-      x = (2.0 * a - b) * sc;
-    }
-    uint16_t p3[TMAX];
-    split_f64<F>(x, p3);
-    for (int t = 0; t < TMAX; ++t) Ws[t * plane + idx] = p3[t];
-  }
-}
-
 // largest |v| as the bit pattern of a non-negative double (atomicMax on the bits)
 __global__ void absmax_kernel(size_t n, const double *__restrict__ x, unsigned long long *out) {
   double m = 0.0;
@@ -266,73 +92,30 @@ __global__ void absmax_kernel(size_t n, const double *__restrict__ x, unsigned l
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// Gs[set][t][c][r][s]: set 0 = G(tau)^T (GT[l][k] = G[k][l]),
-//                      set 1 = Gbar = G(-tau) = -G(tau_{M-k}) (Gbar[p][q]).
-// Slot c holds the time points c*B + b (b < B) of the chunk in its diagonal
-// blocks of N.  FP16: every slot matrix is scaled by its own 2^ex[set][c];
-// block (c, 0) also sets the T1 exponent ex[kExpT1][c] from the bound
-// |T1| <= vmax_s * max_l sum_k |G_s[k][l]| (vmax_s: largest |v| after its
-// scale) and clears the T2/T3 maxima of slot c.
-template <int F>
-__global__ void split_g_kernel(int N, int B, int M, int k0, int count, int C, const double *__restrict__ G,
-                               uint16_t *__restrict__ Gs, int *__restrict__ ex, double vmax_s) {
-  const int c = blockIdx.x, set = blockIdx.y;
-  const size_t plane = (size_t)C * NP * NP;
-  auto elem = [&](int r, int s) -> double {  // entry (r, s) of the slot matrix
-    const int b = r / N;
-    if (b >= B || s / N != b || c * B + b >= count) return 0.0;
-    const int k = k0 + c * B + b, rr = r - b * N, ss = s - b * N;
-    return set == 0 ? G[(size_t)k * N * N + (size_t)ss * N + rr] : -G[(size_t)(M - k) * N * N + (size_t)rr * N + ss];
-  };
-  double sc = 1.0;
-  if constexpr (F != 0) {
-    __shared__ double red[2][32];
-    double m = 0.0, cs = 0.0;  // largest |entry|, largest row sum of |GT| (a column sum of |G|)
-    for (int r4 = threadIdx.x; r4 < NP * 4; r4 += blockDim.x) {  // four threads per row, 16 entries each
-      const int r = r4 >> 2, q0 = (r4 & 3) * 16;
-      double a = 0.0;
-      for (int q = q0; q < q0 + 16; ++q) {
-        const double x = fabs(elem(r, q));
-        a += x;
-        m = fmax(m, x);
-      }
-      a += __shfl_xor_sync(0xffffffffu, a, 1);
-      a += __shfl_xor_sync(0xffffffffu, a, 2);
-      cs = fmax(cs, a);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x / 32] = m;
-      red[1][threadIdx.x / 32] = cs;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)blockDim.x / 32; ++w) {
-        m = fmax(m, red[0][w]);
-        cs = fmax(cs, red[1][w]);
-      }
-      red[0][0] = m;
-      red[1][0] = cs;
-    }
-    __syncthreads();
-    const int e = fp16_exponent(red[0][0]);
-    sc = ldexp(1.0, e);
-    if (threadIdx.x == 0) {
-      ex[set * C + c] = e;
-      if (set == 0) {
-        ex[kExpT1 * C + c] = fp16_exponent(vmax_s * red[1][0] * sc);
-        ex[kMaxT2 * C + c] = 0;
-        ex[kMaxT3 * C + c] = 0;
-      }
-    }
+// largest |v[i][m][q][k] - v[q][k][i][m]| (the pair symmetry (im|qk) = (qk|im)),
+// as the bit pattern of a non-negative double
+__global__ void pair_asym_kernel(int N, const double *__restrict__ v, unsigned long long *out) {
+  const size_t n2 = (size_t)N * N, n4 = n2 * n2;
+  double m = 0.0;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n4; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t a = idx / n2, b = idx % n2;  // a = (i, m), b = (q, k)
+    m = fmax(m, fabs(v[idx] - v[b * n2 + a]));
   }
-  for (int e = threadIdx.x; e < NP * NP; e += blockDim.x) {
-    uint16_t p[TMAX];
-    split_f64<F>(elem(e / NP, e % NP) * sc, p);
-    for (int t = 0; t < TMAX; ++t) Gs[(size_t)(set * TMAX + t) * plane + (size_t)c * NP * NP + e] = p[t];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// v <- the pair-symmetric part (v[i][m][q][k] + v[q][k][i][m]) / 2, in place
+// (each unordered pair of (i,m), (q,k) handled by one thread)
+__global__ void pair_symmetrize_kernel(int N, double *__restrict__ v) {
+  const size_t n2 = (size_t)N * N, n4 = n2 * n2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n4; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t a = idx / n2, b = idx % n2;
+    if (a < b) {
+      const double x = 0.5 * (v[idx] + v[b * n2 + a]);
+      v[idx] = x;
+      v[b * n2 + a] = x;
+    }
   }
 }
 
@@ -559,14 +342,6 @@ __global__ void __launch_bounds__(320, 1)
 // epilogue adds the T blocks -- half the MMA instructions of one product per
 // instruction, with wider N.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-  const float s = __fadd_rn(hi, x);
-  const float bp = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-  hi = s;
-  lo = __fadd_rn(lo, e);
-}
-
 template <int T, int KSUB, int F>
 __global__ void __launch_bounds__(448, 1)
     contract_kernel(const __grid_constant__ CUtensorMap map_t3, const __grid_constant__ CUtensorMap map_w,
@@ -780,6 +555,39 @@ __global__ void __launch_bounds__(448, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Units of the sandwich.  With the pair symmetry of the integrals,
+// v[i][m][q][k] = v[q][k][i][m] ((im|qk) = (qk|im)), the stage-2 intermediate is
+// symmetric under the simultaneous exchange i <-> q, l <-> n:
+//   T2[i][q][l][n] = sum_{m,k} v[i][m][q][k] G[k][l] G[m][n]
+//                  = sum_{m,k} v[q][k][i][m] G[k][l] G[m][n] = T2[q][i][n][l],
+// so the 64 x 64 (l, n) tile of (i, q) is the transpose of the tile of (q, i).
+// A symmetric run computes only the units (i, q pair) with q pair >= i / 2
+// (1056 of 2048 per time-point pair): each writes its two tiles in place and,
+// when q pair > i / 2, also their transposes as the tiles of (q, i); every tile
+// of T2 is then written exactly once.
+// ---------------------------------------------------------------------------
+constexpr int kSymUnitsPerPair = NP * (NP / 2) - (NP / 2) * (NP / 2 - 1);  // 1056 for NP = 64
+
+__device__ __forceinline__ void sandwich_unit(int u, int sym, int &cp, int &i, int &qp) {
+  if (!sym) {
+    cp = u / (NP * 32);
+    i = (u / 32) % NP;
+    qp = u % 32;
+    return;
+  }
+  cp = u / kSymUnitsPerPair;
+  int w = u % kSymUnitsPerPair, a = 0;
+  // the i pair (2a, 2a+1) owns 2 (32 - a) units, i.e. 64 a - a (a - 1) before it
+  while (a < NP / 2 - 1 && w >= 2 * (NP / 2 - a)) {
+    w -= 2 * (NP / 2 - a);
+    ++a;
+  }
+  const int per_i = NP / 2 - a;
+  i = 2 * a + w / per_i;
+  qp = a + w % per_i;
+}
+
+// ---------------------------------------------------------------------------
 // stages 1+2 fused: T2[c][i][q][l][n] = sum_{m,k} G[m][n] v[i][m][q][k] G[k][l]
 //
 // Unit = (tau pair, i, q pair).  MMA1 covers both time points at once: its B
@@ -794,7 +602,7 @@ template <int T, int F>
 __global__ void __launch_bounds__(448, 1)
     sandwich_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
                     const __grid_constant__ CUtensorMap map_t2s, int C, int S, int sl0, int n_units,
-                    int *__restrict__ ex, int *err) {
+                    int *__restrict__ ex, int *err, int sym, float *__restrict__ t2) {
   constexpr int GS = 1;                  // buffered G sets (a tau pair each; a CTA meets one or two)
   constexpr int A1S = (T == 2) ? 2 : 1;  // buffered v tiles (MMA1 consumes them first)
   constexpr int A2S = 2;                 // buffered MMA2 operands: epilogue 1 overlaps MMA2
@@ -848,7 +656,8 @@ __global__ void __launch_bounds__(448, 1)
     const uint64_t keep_pol = tc::policy_evict_last();
     int it = 0, cur_cp = -1, gcount = 0;
     for (int u = u_begin; u < u_end; ++u, ++it) {
-      const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
+      int cp, i, qp;
+      sandwich_unit(u, sym, cp, i, qp);
       if (cp != cur_cp) {
         const int gs = gcount % GS;
         if (gcount >= GS && !tc::mbar_wait(&g_empty[gs], ((gcount / GS) - 1) & 1, abort)) { raise_abort(abort, err); break; }
@@ -892,8 +701,9 @@ __global__ void __launch_bounds__(448, 1)
       tc::mma_commit(&d2_full[db]);
       return true;
     };
+    const int upp = sym ? kSymUnitsPerPair : NP * 32;  // units per time-point pair
     for (int u = u_begin; u < u_end && ok; ++u, ++it) {
-      const int cp = u / (NP * 32);
+      const int cp = u / upp;
       if (cp != cur_cp) {
         if (pend_u >= 0) {  // finish the previous pair before its G set can be recycled
           if (!issue_mma2(2 * pend_u, pend_gs) || !issue_mma2(2 * pend_u + 1, pend_gs)) {
@@ -945,10 +755,11 @@ __global__ void __launch_bounds__(448, 1)
     // Warps 2-5 convert l = 0..31, warps 10-13 l = 32..63 of the same rows.
     const int wq = warp & 3, row = wq * 32 + lane, hf = warp >= 10 ? 1 : 0;
     const int m = row & 63, ql = row >> 6;
+    const int upp = sym ? kSymUnitsPerPair : NP * 32;
     int it = 0;
     bool ok = true;
     for (int u = u_begin; u < u_end && ok; ++u, ++it) {
-      const int b = it & 1, cp = u / (NP * 32);
+      const int b = it & 1, cp = u / upp;
       if (!tc::mbar_wait(&d1_full[b], (it >> 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
       tc::tc_fence_after();
       for (int s = 0; s < 2; ++s) {
@@ -981,7 +792,9 @@ __global__ void __launch_bounds__(448, 1)
     float run_mx[2] = {0.f, 0.f};  // FP16: largest |T2| of time points 2 run_cp + s seen by this thread
     int run_cp = -1;
     for (int u = u_begin; u < u_end && ok; ++u) {
-      const int cp = u / (NP * 32), i = (u / 32) % NP, qp = u % 32;
+      int cp, i, qp;
+      sandwich_unit(u, sym, cp, i, qp);
+      const bool mirror = sym && qp > i / 2;  // also write the transposed tiles (q, i)
       if (F != 0 && cp != run_cp) {  // one atomic per warp and time point, not per job
         if (run_cp >= 0)
           for (int s = 0; s < 2; ++s) warp_absmax_to(&ex[kMaxT2 * S + sl0 + 2 * run_cp + s], run_mx[s]);
@@ -1024,6 +837,14 @@ __global__ void __launch_bounds__(448, 1)
         tc::fence_proxy_async_smem();  // these writes are read by the TMA store
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&o_full[ob]);
+        if (mirror) {
+          // the transposed tile: T2[c][q][i][n][l] = D2[(ql, l), n], q = 2 qp + ql.
+          // For each n a warp writes 32 consecutive l, one 128-byte line.
+          const int q = 2 * qp + (row >> 6), l = row & 63;
+          float *dst = t2 + ((((size_t)(2 * cp + s) * NP + q) * NP + i) * NP) * NP + l;
+#pragma unroll
+          for (int n = 0; n < 64; ++n) dst[(size_t)n * NP] = v[n];
+        }
         if (warp == 6) {  // the whole warp waits (uniform exit on a timeout); lane 0 issues
           if (!tc::mbar_wait(&o_full[ob], (j / OS) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
           if (lane == 0) {
@@ -1203,35 +1024,6 @@ __global__ void wait_timeout_kernel(int *err) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// bf16 operand tiles use the 128-byte swizzle of the MMA layouts; fp32 tiles
-// (split on chip) are plain row-major
-bool make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-              const uint32_t *box, bool fp32 = false, bool fp32_swizzle = false) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = fn(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank,
-                  const_cast<void *>(base), reinterpret_cast<const cuuint64_t *>(dims),
-                  reinterpret_cast<const cuuint64_t *>(strides_bytes), reinterpret_cast<const cuuint32_t *>(box), es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  (fp32 && !fp32_swizzle) ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 struct TcState {
   int C = 0;                           // slots per chunk (one launch of each tile kernel)
   int S = 0;                           // slots of the whole grid (a multiple of C)
@@ -1273,7 +1065,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
   if (count <= 0) return GF2_OK;
   // every slot of the call split in one launch, the whole output cleared once
   const int n_chunks = (count + C * B - 1) / (C * B);
-  GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<F><<<dim3(n_chunks * C, 2), 256, 0, ctx->stream>>>(
+  GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<NP, F><<<dim3(n_chunks * C, 2), 256, 0, ctx->stream>>>(
                                  N, B, ctx->M, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
   GF2_CK_LAUNCH(ctx, "split_g_kernel");
   GF2_CK(ctx, cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)count * N * N, ctx->stream));
@@ -1281,10 +1073,11 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
     const int cnt = std::min(C * B, count - c0);
     const int ce = (((cnt + B - 1) / B) + 1) & ~1;  // slots, rounded up to whole pairs
     double *out = d_out + (size_t)c0 * N * N;
-    const int u1 = (ce / 2) * NP * 32;
+    const int sym = ctx->tc_pair_sym ? 1 : 0;
+    const int u1 = (ce / 2) * (sym ? kSymUnitsPerPair : NP * 32);
     GF2_PROF(ctx, GF2_K_SANDWICH,
-             (sandwich_kernel<T, F><<<std::min(u1, sms), 448, ssw, ctx->stream>>>(map_v, s->map_g, s->map_t2s, C, S, sl0,
-                                                                                   u1, s->gexp, ctx->d_err)));
+             (sandwich_kernel<T, F><<<std::min(u1, sms), 448, ssw, ctx->stream>>>(
+                 map_v, s->map_g, s->map_t2s, C, S, sl0, u1, s->gexp, ctx->d_err, sym, s->T2)));
     GF2_CK_LAUNCH(ctx, "sandwich_kernel");
     const int u2 = ce * NP * 32;
     GF2_PROF(ctx, GF2_K_XFORM,
@@ -1305,10 +1098,20 @@ TcState *tc_state(gf2_ctx *ctx) { return reinterpret_cast<TcState *>(ctx->d_tc_w
 }  // namespace
 
 gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
-  if (ctx->N > NP) return GF2_ERR_UNSUPPORTED;
+  if (ctx->N > 2 * NP) return GF2_ERR_UNSUPPORTED;
   if (!encode_fn()) return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
-  ctx->tc_pack = ctx->N <= NP / 2 ? NP / ctx->N : 1;
-  const size_t bytes = TMAX * kPlane4 * sizeof(uint16_t);
+  if (ctx->N > NP) {  // 128-wide planes (several GB): built by the first split-precision call
+    ctx->tc_planes_stale = true;
+    return GF2_OK;
+  }
+  return gf2_tc_build_planes(ctx, NP);
+}
+
+// The split term planes of v and W (BF16 and FP16) for tiles of width P (64 or 128)
+gf2_status gf2_tc_build_planes(gf2_ctx *ctx, int P) {
+  ctx->tc_pack = (P == NP && ctx->N <= NP / 2) ? NP / ctx->N : 1;
+  const size_t plane4 = (size_t)P * P * P * P;
+  const size_t bytes = TMAX * plane4 * sizeof(uint16_t);
   if (!ctx->d_v_split) GF2_CK(ctx, cudaMalloc(&ctx->d_v_split, bytes));
   if (!ctx->d_wt_split) GF2_CK(ctx, cudaMalloc(&ctx->d_wt_split, bytes));
   if (!ctx->d_v_split16) GF2_CK(ctx, cudaMalloc(&ctx->d_v_split16, bytes));
@@ -1350,14 +1153,42 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
     vs = vorth;
     vw = vfold;
   }
+  // The symmetric sandwich needs (im|qk) = (qk|im).  Integrals of real orbitals
+  // have it; the orthonormal-basis integrals have it mathematically, so their
+  // rounding-level asymmetry (from the order of the four index transforms) is
+  // removed by averaging the pair-transposed entries.
+  unsigned long long *d_amax = reinterpret_cast<unsigned long long *>(ctx->d_red);
+  GF2_CK(ctx, cudaMemsetAsync(d_amax, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  absmax_kernel<<<blocks, 256, 0, ctx->stream>>>(n4, ctx->d_v, d_amax);
+  GF2_CK_LAUNCH(ctx, "absmax_kernel");
+  pair_asym_kernel<<<blocks, 256, 0, ctx->stream>>>(N, ctx->d_v, d_amax + 2);
+  GF2_CK_LAUNCH(ctx, "pair_asym_kernel");
+  {
+    unsigned long long b3[3] = {0, 0, 0};
+    GF2_CK(ctx, cudaMemcpyAsync(b3, d_amax, sizeof(b3), cudaMemcpyDeviceToHost, ctx->stream));
+    GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    double v0max, asym;
+    std::memcpy(&v0max, &b3[0], sizeof(v0max));
+    std::memcpy(&asym, &b3[2], sizeof(asym));
+    ctx->tc_pair_sym = asym <= 1e-12 * v0max;
+  }
+  if (ctx->tc_pair_sym && vorth) {
+    pair_symmetrize_kernel<<<blocks, 256, 0, ctx->stream>>>(N, vorth);
+    GF2_CK_LAUNCH(ctx, "pair_symmetrize_kernel");
+  }
   const int B = ctx->tc_pack;
-  split_v_kernel<0><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, 0, (uint16_t *)ctx->d_v_split);
+  if (P == NP)
+    split_v_kernel<NP, 0><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, 0, (uint16_t *)ctx->d_v_split);
+  else
+    split_v_kernel<2 * NP, 0><<<blocks, 256, 0, ctx->stream>>>(N, 1, vs, 0, (uint16_t *)ctx->d_v_split);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<0><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, 0, (uint16_t *)ctx->d_wt_split);
+  if (P == NP)
+    split_w_kernel<NP, 0><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, 0, (uint16_t *)ctx->d_wt_split);
+  else
+    split_w_kernel<2 * NP, 0><<<blocks, 256, 0, ctx->stream>>>(N, 1, vw, 0, (uint16_t *)ctx->d_wt_split);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   // FP16 planes: v scaled so that its largest entry lies in [2^13, 2^14); W
   // (|W| <= 3 max|vw|) by the exponent of 3 max|vw|
-  unsigned long long *d_amax = reinterpret_cast<unsigned long long *>(ctx->d_red);
   GF2_CK(ctx, cudaMemsetAsync(d_amax, 0, 2 * sizeof(unsigned long long), ctx->stream));
   absmax_kernel<<<blocks, 256, 0, ctx->stream>>>(n4, vs, d_amax);
   GF2_CK_LAUNCH(ctx, "absmax_kernel");
@@ -1372,9 +1203,15 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
   ctx->e_v16 = fp16_exponent(vmax);
   ctx->e_w16 = fp16_exponent(3.0 * wmax);
   ctx->vmax16 = ldexp(vmax, ctx->e_v16);
-  split_v_kernel<1><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
+  if (P == NP)
+    split_v_kernel<NP, 1><<<blocks, 256, 0, ctx->stream>>>(N, B, vs, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
+  else
+    split_v_kernel<2 * NP, 1><<<blocks, 256, 0, ctx->stream>>>(N, 1, vs, ctx->e_v16, (uint16_t *)ctx->d_v_split16);
   GF2_CK_LAUNCH(ctx, "split_v_kernel");
-  split_w_kernel<1><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
+  if (P == NP)
+    split_w_kernel<NP, 1><<<blocks, 256, 0, ctx->stream>>>(N, B, vw, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
+  else
+    split_w_kernel<2 * NP, 1><<<blocks, 256, 0, ctx->stream>>>(N, 1, vw, ctx->e_w16, (uint16_t *)ctx->d_wt_split16);
   GF2_CK_LAUNCH(ctx, "split_w_kernel");
   if (vorth) {
     GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1382,6 +1219,7 @@ gf2_status gf2_tc_prepare_integrals(gf2_ctx *ctx) {
     cudaFree(vfold);
   }
   ctx->split_terms = TMAX;
+  ctx->tc_planes_stale = false;
   return GF2_OK;
 }
 
@@ -1474,6 +1312,7 @@ static gf2_status tc_workspace(gf2_ctx *ctx) {
 }
 
 void gf2_tc_release(gf2_ctx *ctx) {
+  gf2_tc128_release(ctx);
   TcState *s = tc_state(ctx);
   if (!s) return;
   cudaFree(s->Gs);
@@ -1485,9 +1324,11 @@ void gf2_tc_release(gf2_ctx *ctx) {
 }
 
 gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, double *d_out, int prec) {
-  if (ctx->N > NP || !ctx->d_v_split)
-    return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "tensor-core path needs N <= 64 and gf2_set_integrals");
-  gf2_status st = tc_workspace(ctx);
+  if (ctx->N > 2 * NP) return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "tensor-core path needs N <= 128");
+  gf2_status st;
+  if (ctx->N > NP && ctx->tc_planes_stale && (st = gf2_tc_build_planes(ctx, 2 * NP)) != GF2_OK) return st;
+  if (!ctx->d_v_split) return gf2_fail(ctx, GF2_ERR_UNSUPPORTED, "tensor-core path needs gf2_set_integrals");
+  st = ctx->N > NP ? gf2_tc128_workspace(ctx) : tc_workspace(ctx);
   if (st != GF2_OK) return st;
   GF2_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
   TcState *s = tc_state(ctx);
@@ -1501,11 +1342,15 @@ gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G, int k0, int count, doub
     G_use = Go;
     out_use = ctx->d_orth_ws + 2 * (size_t)ctx->n_tau * ctx->N * ctx->N;
   }
-  switch (prec) {
-    case GF2_PREC_BF16X3: st = run_chunks<2, 0>(ctx, s, G_use, k0, count, out_use); break;
-    case GF2_PREC_BF16X6: st = run_chunks<3, 0>(ctx, s, G_use, k0, count, out_use); break;
-    case GF2_PREC_FP16X3: st = run_chunks<2, 1>(ctx, s, G_use, k0, count, out_use); break;
-    default: st = run_chunks<3, 1>(ctx, s, G_use, k0, count, out_use); break;
+  if (ctx->N > NP) {
+    st = gf2_tc128_run(ctx, G_use, k0, count, out_use, prec);
+  } else {
+    switch (prec) {
+      case GF2_PREC_BF16X3: st = run_chunks<2, 0>(ctx, s, G_use, k0, count, out_use); break;
+      case GF2_PREC_BF16X6: st = run_chunks<3, 0>(ctx, s, G_use, k0, count, out_use); break;
+      case GF2_PREC_FP16X3: st = run_chunks<2, 1>(ctx, s, G_use, k0, count, out_use); break;
+      default: st = run_chunks<3, 1>(ctx, s, G_use, k0, count, out_use); break;
+    }
   }
   if (st != GF2_OK) return st;
   if (ctx->d_Shalf) {  // the row index: Sigma[b] = S^1/2 X[b]

@@ -101,9 +101,9 @@ def test_tail_dyson_density_energy_at_largest_bases(g, n):
 
 @pytest.mark.parametrize("n", [112, N_MAX])
 def test_sigma_fp64_and_fock_at_largest_basis(g, n):
-    """One grid point of Eq. Sigma on the FP64 path and Eq. FockMatrix at
-    N = 128 (two full 64-wide GEMM tiles in every stage), and at N = 112 (a
-    48-wide ragged tile)."""
+    """One grid point of Eq. Sigma on the FP64 path (and on the 128-wide
+    split tensor-core path) and Eq. FockMatrix at N = 128 (two full 64-wide
+    GEMM tiles in every stage), and at N = 112 (a 48-wide ragged tile)."""
     n_tau, k = 9, 3
     v = gi.random_eri(n, seed=5) * 0.1
     G = gi.random_symmetric_g(n, n_tau, seed=6)
@@ -120,14 +120,16 @@ def test_sigma_fp64_and_fock_at_largest_basis(g, n):
         Fd = torch.zeros(n, n, dtype=torch.float64, device="cuda")
         g.gf2_fock(ctx.handle, dev(h), dev(P), Fd)
         got, got_F = host(out)[0], host(Fd)
-        # the tensor-core path is limited to 64-wide bases and says so
-        with pytest.raises(g.GF2Error):
-            g.gf2_sigma_tau_points(ctx.handle, dev(G), k, 1, out, g.GF2_PREC_BF16X6)
-        # the context stays usable after the refusal
+        # the 128-wide tensor-core pipeline on the same point and context
+        out_tc = torch.zeros_like(out)
+        g.gf2_sigma_tau_points(ctx.handle, dev(G), k, 1, out_tc, g.GF2_PREC_BF16X6)
+        got_tc = host(out_tc)[0]
+        # the FP64 path again after the split one: the context's state is intact
         out2 = torch.zeros_like(out)
         g.gf2_sigma_tau_points(ctx.handle, dev(G), k, 1, out2, g.GF2_PREC_FP64)
         again = host(out2)[0]
     assert np.abs(again - got).max() <= 1e-13 * np.abs(got).max()
+    assert np.abs(got_tc - ref).max() <= 4e-6 * np.abs(ref).max()
     # FP64 sums of up to N^3 = 2.1e6 products per entry in another order than numpy's
     assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
     assert np.abs(got_F - F_ref).max() <= 1e-12 * max(1.0, np.abs(F_ref).max())

@@ -21,6 +21,7 @@ scaled) and a per-kernel breakdown are reported beside it.
   python bench.py --workload batch   # batched Sigma(tau) over 24 systems, N = 4 .. 50
   python bench.py --workload h32_sto3g   # N = 32 lattice at 1.4 / 2.0 / 3.0 bohr: split vs FP64
   python bench.py --workload converge    # GF2 to convergence on the H10 chain, split vs FP64
+  python bench.py --workload h64         # H64 lattice (N = 128), the 128-wide split Sigma
 
 The batch workload has the sizes of a multi-system study: linear H_n chains,
 n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
@@ -65,7 +66,7 @@ def parse():
     ap.add_argument("--ref-points", type=int, default=4, help="tau points per step of --impl reference")
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
-    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "batch", "h32_sto3g", "converge"])
+    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge"])
     ap.add_argument("--max-outer", type=int, default=30, help="outer GF2 iterations of --workload converge")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
@@ -772,6 +773,162 @@ def run_h32_sto3g(args, rank, world, dist):
         print(json.dumps(line))
 
 
+def first_step_gpu(g, h, s, r, N, n_tau, n_iw, beta, prec, mu_hf=None):
+    """The benchmark's step on an open context: finite-temperature HF state,
+    G(i w) -> G(tau), Eq. Sigma, Sigma -> Sigma(i w), mu search at F_HF, energy.
+    Returns (E, P, mu_hf, G_tau)."""
+    import torch
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    S, hc, F0 = f64(s.S), f64(s.h), f64(r.F)
+    G0 = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    P0 = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+    if mu_hf is None:
+        mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+    mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G0, P0)
+    mom = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+    G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    g.gf2_tail_moments(h, S, F0, mu_hf, None, mom)
+    g.gf2_fft_iw_to_tau(h, G0, mom, G_tau)
+    Sig = torch.empty_like(G_tau)
+    g.gf2_sigma_tau(h, G_tau, Sig, prec)
+    Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+    g.gf2_fft_tau_to_iw(h, Sig, Sig_iw, sig12)
+    del Sig
+    P = torch.empty_like(P0)
+    g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, G0, P)
+    e1, e2 = g.gf2_energy(h, hc, F0, P, S, G0, Sig_iw, sig12)
+    return s.e_nuc + e1 + e2, P, mu_hf, G_tau
+
+
+def run_h64(args, rank, world, dist):
+    """H64 4x4x4 lattice at 2.0 bohr, 6-31G (N = 128), beta = 200, n_tau = 8193,
+    n_iw = 16384: one GF2 step through every row with the 128-wide split Sigma
+    (time points in chunks of 16, intermediates 2 x 16 GB).  Accuracy: split vs
+    FP64 GPU Sigma on sampled points of the full grid, and the first-step
+    energy and density of the split path against the FP64 GPU path on a
+    reduced grid (129 time points, 256 frequencies; the FP64 Sigma of the full
+    grid would take about 30 minutes).  The FP64 GPU path itself is checked
+    against the oracle at N = 128 by the GPU tests."""
+    import torch
+    import gf2_inputs as gi
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    s = gi.build_system("h64_lattice_631g")
+    r = gi.rhf(s)
+    N, beta = s.nbf, 200.0
+    n_tau, n_iw = args.n_tau or 8193, args.n_iw or 16384
+    prec = PRECS[args.prec]
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    S, hcore, F0 = f64(s.S), f64(s.h), f64(r.F)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ctx = g.Context(N, n_tau, n_iw, beta)
+    h = ctx.handle
+    g.gf2_set_integrals(h, f64(s.eri))
+    g.gf2_set_overlap(h, S)
+    G_iw0 = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    P0 = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+    mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+    mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G_iw0, P0)
+    moments = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+    G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+    G_iw = torch.empty_like(G_iw0)
+    P = torch.empty_like(P0)
+    F_new = torch.empty_like(F0)
+
+    def step(out, sev=None):
+        g.gf2_tail_moments(h, S, F0, mu_hf, None, moments)
+        g.gf2_fft_iw_to_tau(h, G_iw0, moments, G_tau)
+        if sev:
+            sev[0].record(stream)
+        g.gf2_sigma_tau(h, G_tau, Sig_tau, prec)
+        if sev:
+            sev[1].record(stream)
+        g.gf2_fft_tau_to_iw(h, Sig_tau, Sig_iw, sig12)
+        mu, nev = g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, G_iw, P)
+        g.gf2_fock(h, hcore, P, F_new)
+        e1, e2 = g.gf2_energy(h, hcore, F0, P, S, G_iw, Sig_iw, sig12)
+        out.append((s.e_nuc + e1 + e2, mu, nev))
+
+    log = []
+    for _ in range(args.warmup):
+        step(log)
+    torch.cuda.synchronize()
+    g.gf2_profile(h, True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t0, t1 = ev(), ev()
+    sev = [(ev(), ev()) for _ in range(args.steps)]
+    t0.record(stream)
+    for k in range(args.steps):
+        step(log, sev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof, launches = g.gf2_profile_report(h)
+    g.gf2_profile(h, False)
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, dist)
+    sigma_ms = statistics.mean(a.elapsed_time(b) for a, b in sev)
+    useful = 8.0 * N ** 5 * n_tau
+    issued = ISSUED[args.prec]
+    _, bf16_burst, bf16_sust, peak_kind = measured_peaks()
+    # split vs FP64 GPU Sigma on sampled points of the full grid
+    pts = [1, 2, n_tau // 4, n_tau // 2, n_tau - 3]
+    o64 = torch.empty(1, N, N, dtype=torch.float64, device="cuda")
+    osp = torch.empty_like(o64)
+    worst, t64 = 0.0, []
+    for k in pts:
+        a, b = ev(), ev()
+        a.record(stream)
+        g.gf2_sigma_tau_points(h, G_tau, k, 1, o64, 0)
+        b.record(stream)
+        g.gf2_sigma_tau_points(h, G_tau, k, 1, osp, prec)
+        torch.cuda.synchronize()
+        t64.append(a.elapsed_time(b))
+        rel = ((osp - o64).abs().max() / o64.abs().max()).item()
+        worst = max(worst, rel)
+    fp64_s_per_iter = statistics.median(t64) * 1e-3 * n_tau
+    prof_ms = {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in prof.items()}
+    ctx.close()
+    del G_iw0, G_iw, Sig_iw, Sig_tau
+    torch.cuda.empty_cache()
+    # the same step on a reduced grid: split and FP64 GPU Sigma
+    reduced = {}
+    with g.Context(N, 129, 256, beta) as c2:
+        g.gf2_set_integrals(c2.handle, f64(s.eri))
+        g.gf2_set_overlap(c2.handle, S)
+        E64, P64, _, _ = first_step_gpu(g, c2.handle, s, r, N, 129, 256, beta, 0)
+        for name in sorted({args.prec, "fp16x3", "bf16x6"}):
+            Es, Ps, _, _ = first_step_gpu(g, c2.handle, s, r, N, 129, 256, beta, PRECS[name])
+            reduced[name] = {"abs_dE_vs_fp64_gpu": abs(Es - E64), "max_abs_dP": (Ps - P64).abs().max().item()}
+    line = {"metric": "Σ(τ) s/iter & TFLOP/s at N=128 (H64 lattice): split vs FP64 GPU path",
+            "value": useful / (ms_step * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+            "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
+            "config": {"workload": f"H64 lattice 4x4x4 at 2.0 bohr, 6-31G (N=128), beta=200, n_tau={n_tau}, n_iw={n_iw}",
+                       "step": "one GF2 outer iteration, all hot-path rows",
+                       "l2": "inputs larger than L2 (G(iw) 4.3 GB, intermediates 32 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "sigma": {"s_per_iter": sigma_ms * 1e-3, "tflops_useful": useful / (sigma_ms * 1e-3) / 1e12,
+                      "tflops_issued": useful * issued / (sigma_ms * 1e-3) / 1e12,
+                      "issued_frac_of_bf16_sustained": useful * issued / (sigma_ms * 1e-3) / 1e12 / bf16_sust,
+                      "peak_source": f"{peak_kind} sustained BF16 {bf16_sust} TFLOP/s (MEASURED_PEAKS.json)"},
+            "fp64_gpu_path": {"sigma_s_per_iter": fp64_s_per_iter, "sample": f"points {pts}"},
+            "speedup_split_vs_fp64_sigma": fp64_s_per_iter / (sigma_ms * 1e-3),
+            "kernels": prof_ms, "gpu_launches": launches, "clocks": clocks,
+            "mu_evaluations_per_step": log[-1][2],
+            "accuracy": {"split_vs_fp64_gpu_sigma_max_rel": worst, "sampled_points": pts,
+                         "reduced_grid_first_step": {"grid": "n_tau=129, n_iw=256", **reduced}}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_converge(args, rank, world, dist):
     """Self-consistent GF2 on the linear H10 chain (STO-3G, 1.8 bohr, beta = 100,
     n_tau = 2049, n_iw = 4096) until the energy changes by less than 1e-8 Eh between
@@ -826,6 +983,8 @@ def main():
         run_h32_sto3g(args, rank, world, dist)
     elif args.workload == "converge":
         run_converge(args, rank, world, dist)
+    elif args.workload == "h64":
+        run_h64(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -22,6 +22,7 @@ scaled) and a per-kernel breakdown are reported beside it.
   python bench.py --workload h32_sto3g   # N = 32 lattice at 1.4 / 2.0 / 3.0 bohr: split vs FP64
   python bench.py --workload converge    # GF2 to convergence on the H10 chain, split vs FP64
   python bench.py --workload h64         # H64 lattice (N = 128), the 128-wide split Sigma
+  python bench.py --workload sigma --n-bf 128 --n-tau 33   # the Sigma build alone (kernel profiles)
 
 The batch workload has the sizes of a multi-system study: linear H_n chains,
 n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
@@ -66,7 +67,9 @@ def parse():
     ap.add_argument("--ref-points", type=int, default=4, help="tau points per step of --impl reference")
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
-    ap.add_argument("--workload", default="h32_631g", choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge"])
+    ap.add_argument("--workload", default="h32_631g",
+                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma"])
+    ap.add_argument("--n-bf", type=int, default=128, help="basis size of --workload sigma")
     ap.add_argument("--max-outer", type=int, default=30, help="outer GF2 iterations of --workload converge")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
@@ -405,7 +408,12 @@ def run_ours(args, rank, world, dist):
     # multiply divide the BF16 peak), and the bytes of the stage's own FP32
     # intermediates (T2 written by stages 1+2, T2 read and T3 written by stage 3,
     # T3 read by stage 4), reported beside the roofline as implementation traffic.
-    tensor_work = {"sigma_sandwich": (4.0 * N ** 5 * C, 4.0 * n4 * C),
+    # with the pair symmetry (im|qk) = (qk|im) of v the sandwich computes only the
+    # unique (i, q) tiles of the stage-2 intermediate (1056 of 2048 units per pair
+    # of time points) and mirrors the rest: its work is counted as computed
+    pair_sym = bool(np.abs(s.eri - s.eri.transpose(2, 3, 0, 1)).max() <= 1e-12 * np.abs(s.eri).max())
+    sym_frac = 1056.0 / 2048.0 if pair_sym else 1.0
+    tensor_work = {"sigma_sandwich": (4.0 * N ** 5 * C * sym_frac, 4.0 * n4 * C),
                    "sigma_xform": (2.0 * N ** 5 * C, 8.0 * n4 * C),
                    "sigma_contract": (2.0 * N ** 5 * C, 4.0 * n4 * C)}
     # kernels whose every launch covers the full problem (per-launch averages are
@@ -480,6 +488,7 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
         "config": config_of(world),
         "sigma": {"s_per_iter": sigma_ms * 1e-3, "tflops_useful": sigma_tflops,
+                  "stage2_pair_symmetry": pair_sym,
                   "tensor_kernels_ms": tc_ms, "tflops_issued": sigma_tflops * issued_factor,
                   # split products issued against the sustained BF16 peak: over the whole
                   # build (including its FP64 basis transforms) and over the three tensor kernels
@@ -929,6 +938,42 @@ def run_h64(args, rank, world, dist):
         print(json.dumps(line))
 
 
+def run_sigma_only(args, rank, world, dist):
+    """The Sigma(tau) build alone on seeded random inputs (a real symmetric
+    G(tau) per point and 8-fold symmetric integrals) of --n-bf basis functions
+    and --n-tau time points: the case the kernel profiles are taken on."""
+    import torch
+    import gf2_inputs as gi
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    N, n_tau = args.n_bf, args.n_tau or 33
+    prec = PRECS[args.prec]
+    G = torch.as_tensor(gi.random_symmetric_g(N, n_tau, seed=11) * 0.3, device="cuda")
+    v = torch.as_tensor(gi.random_eri(N, seed=12), device="cuda")
+    out = torch.empty_like(G)
+    stream = torch.cuda.current_stream()
+    with g.Context(N, n_tau, 8, 10.0) as ctx:
+        g.gf2_set_integrals(ctx.handle, v)
+        for _ in range(args.warmup):
+            g.gf2_sigma_tau(ctx.handle, G, out, prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            g.gf2_sigma_tau(ctx.handle, G, out, prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    useful = 8.0 * N ** 5 * n_tau
+    _, _, bf16_sust, _ = measured_peaks()
+    if rank == 0:
+        print(json.dumps({"metric": f"Σ(τ) build only, N={N}, {n_tau} time points", "value": useful / (ms * 1e-3) / 1e12,
+                          "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                          "dtype": args.prec, "data": "synthetic (seeded random G(tau) and integrals)",
+                          "issued_frac_of_bf16_sustained": useful * ISSUED[args.prec] / (ms * 1e-3) / 1e12 / bf16_sust}))
+
+
 def run_converge(args, rank, world, dist):
     """Self-consistent GF2 on the linear H10 chain (STO-3G, 1.8 bohr, beta = 100,
     n_tau = 2049, n_iw = 4096) until the energy changes by less than 1e-8 Eh between
@@ -985,6 +1030,8 @@ def main():
         run_converge(args, rank, world, dist)
     elif args.workload == "h64":
         run_h64(args, rank, world, dist)
+    elif args.workload == "sigma":
+        run_sigma_only(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist:

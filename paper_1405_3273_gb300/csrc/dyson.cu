@@ -26,6 +26,24 @@ enum { SL_SINV = GF2_SL_SINV, SL_A1 = GF2_SL_A1, SL_A2 = GF2_SL_A2, SL_A3 = GF2_
        SL_B1 = GF2_SL_B1, SL_B2 = GF2_SL_B2, SL_B3 = GF2_SL_B3, SL_T1 = GF2_SL_T1, SL_TMP = GF2_SL_TMP,
        SL_MOM = GF2_SL_MOM, SL_COEF = GF2_SL_COEF, SL_MISC = GF2_SL_MISC };
 
+// State of the device-resident chemical-potential search (step 2.a): the point
+// to evaluate next and the bracket / Brent variables, updated by one thread
+// after every count evaluation (see mu_control_kernel).
+struct MuState {
+  double n_elec, tol, tol_coarse;   // inputs
+  int max_iter, cap_coarse, n_iw, n_coarse;
+  double mu;                        // next point to evaluate
+  int nf;                           // frequencies of that evaluation
+  int stage;                        // 0 coarse, 1 full, 2 done
+  int status;                       // 0 running, 1 found, 2 not converged, 3 non-finite count, 4 vanishing pivot
+  int evals;
+  double mu_out;
+  int phase;                        // 0 first point, 1 bracketing upward, 2 downward, 3 Brent
+  int n, cap, have_prev;
+  double slope_hint, tol_f, step, lo, hi, flo, fhi, a, b, c, fa, fb, fc, d, e;
+  double last_mu, last_f, prev_mu, prev_f;
+};
+
 __global__ void pole_coef_kernel(int N2, double a, const double *mom, double *coef) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N2) return;
@@ -36,9 +54,10 @@ __global__ void pole_coef_kernel(int N2, double a, const double *mom, double *co
   coef[3 * N2 + e] = g4 - 3.0 * a * g3 + 3.0 * a * a * g2 - a * a * a * g1;
 }
 
-__global__ void moments_kernel(int N2, double mu, const double *basis, double *mom) {
+__global__ void moments_kernel(int N2, double mu, const double *basis, double *mom, const MuState *st = nullptr) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N2) return;
+  if (st) mu = st->mu;
   const double A0 = basis[SL_SINV * N2 + e], A1 = basis[SL_A1 * N2 + e];
   const double A2 = basis[SL_A2 * N2 + e], A3 = basis[SL_A3 * N2 + e];
   const double B1 = basis[SL_B1 * N2 + e], B2 = basis[SL_B2 * N2 + e], B3 = basis[SL_B3 * N2 + e];
@@ -65,7 +84,12 @@ constexpr int kDysonMaxPerThread = (GF2_MAX_N * (GF2_MAX_N + 1) / 2 + kDysonThre
 template <int PER, int MINB>
 __global__ void __launch_bounds__(kDysonThreads, MINB)
     dyson_kernel(int N, double beta, double mu, const double *__restrict__ S, const double *__restrict__ F,
-                 const double2 *__restrict__ Sig, double2 *__restrict__ G, int *flag) {
+                 const double2 *__restrict__ Sig, double2 *__restrict__ G, int *flag,
+                 const MuState *st = nullptr) {
+  if (st) {  // the device-resident search: mu and the frequency count come from its state
+    if ((int)blockIdx.x >= st->nf) return;
+    mu = st->mu;
+  }
   __shared__ double2 v[GF2_MAX_N];  // pivot column a_ik
   __shared__ double2 w[GF2_MAX_N];  // a_ik / a_kk
   __shared__ double2 pinv;
@@ -153,10 +177,14 @@ __global__ void __launch_bounds__(kDysonThreads, MINB)
 
 // partial[chunk][e] = sum_{n in chunk} Re G_e(n)
 __global__ void density_partial_kernel(int N2, int n_iw, int chunk, const double2 *__restrict__ G,
-                                       double *__restrict__ partial) {
+                                       double *__restrict__ partial, const MuState *st = nullptr) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N2) return;
   const int c = blockIdx.y;
+  if (st) {
+    n_iw = st->nf;
+    if (c * chunk >= n_iw) return;
+  }
   const int n0 = c * chunk, n1 = min(n_iw, n0 + chunk);
   double acc = 0.0;
   for (int n = n0; n < n1; ++n) acc += G[(size_t)n * N2 + e].x;
@@ -166,9 +194,14 @@ __global__ void density_partial_kernel(int N2, int n_iw, int chunk, const double
 // P_e = (4/beta) [sum_n Re G_e - sum_r c_r R_r] - 2 sum_r c_r g_r(beta)
 __global__ void density_final_kernel(int N2, int nchunks, double beta, const double *partial,
                                      const double *coef, const double *pole_resum,
-                                     const double *tau_pole_beta, double *P) {
+                                     const double *tau_pole_beta, double *P, const MuState *st = nullptr,
+                                     const double *pole_resum_coarse = nullptr) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N2) return;
+  if (st) {  // chunks of 256 frequencies over the evaluation's range, its tail sums
+    nchunks = (st->nf + 255) / 256;
+    if (st->stage == 0) pole_resum = pole_resum_coarse;
+  }
   double s = 0.0;
   for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * N2 + e];
   double tail_sum = 0.0, tail_beta = 0.0;
@@ -195,6 +228,186 @@ __global__ void trace_kernel(int N, const double *P, const double *S, double *ou
     __syncthreads();
   }
   if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident chemical-potential search.  One evaluation of the count
+// N(mu) - n_elec (moments, pole coefficients, Dyson, density, trace) is the
+// body of a CUDA-graph WHILE loop; after it, mu_control_kernel (one thread)
+// takes the decision the host would take -- bracket outward from the start,
+// then Brent's method (inverse quadratic interpolation or secant steps with
+// bisection safeguards, Brent 1973, "Algorithms for Minimization without
+// Derivatives", ch. 4), first on the count over the lowest n_iw/8 frequencies
+// and then on the full count -- writes the next mu into the state, and ends
+// the loop when the tolerance is met, the evaluation cap is reached or a count
+// is not finite.  The host reads the state once, after the graph.
+// ---------------------------------------------------------------------------
+__device__ void mu_solve_begin(MuState *s, double mu0, double slope_hint, double tol_f, int cap, int nf) {
+  s->phase = 0;
+  s->n = 0;
+  s->have_prev = 0;
+  s->slope_hint = slope_hint;
+  s->tol_f = tol_f;
+  s->cap = cap;
+  s->nf = nf;
+  s->mu = mu0;
+}
+
+// the end of one solve (coarse or full): the last point, found or not
+__device__ void mu_solve_end(MuState *s, bool found) {
+  const double slope =
+      (s->have_prev && s->last_mu != s->prev_mu) ? (s->last_f - s->prev_f) / (s->last_mu - s->prev_mu) : 0.0;
+  if (s->stage == 0) {  // coarse: the full search starts at its root, with its slope
+    const double mu_start = (found && isfinite(s->last_mu)) ? s->last_mu : s->mu_out;
+    s->stage = 1;
+    mu_solve_begin(s, mu_start, found ? slope : 0.0, s->tol, s->max_iter, s->n_iw);
+  } else {
+    s->mu_out = s->last_mu;
+    s->status = found ? 1 : 2;
+    s->stage = 2;
+  }
+}
+
+// one Brent step on the bracket [b, c]: sets the next point, or ends the solve
+__device__ void mu_brent_next(MuState *s) {
+  if (s->n >= s->cap) {
+    mu_solve_end(s, false);
+    return;
+  }
+  if ((s->fb > 0.0) == (s->fc > 0.0)) {
+    s->c = s->a;
+    s->fc = s->fa;
+    s->d = s->e = s->b - s->a;
+  }
+  if (fabs(s->fc) < fabs(s->fb)) {
+    s->a = s->b; s->b = s->c; s->c = s->a;
+    s->fa = s->fb; s->fb = s->fc; s->fc = s->fa;
+  }
+  const double tol1 = 2.0 * 2.2e-16 * fabs(s->b) + 1e-16;
+  const double xm = 0.5 * (s->c - s->b);
+  if (fabs(xm) <= tol1) {  // bracket collapsed without reaching the tolerance
+    mu_solve_end(s, false);
+    return;
+  }
+  if (fabs(s->e) >= tol1 && fabs(s->fa) > fabs(s->fb)) {
+    const double sq = s->fb / s->fa;
+    double p, q;
+    if (s->a == s->c) {
+      p = 2.0 * xm * sq;
+      q = 1.0 - sq;
+    } else {
+      const double qq = s->fa / s->fc, r = s->fb / s->fc;
+      p = sq * (2.0 * xm * qq * (qq - r) - (s->b - s->a) * (r - 1.0));
+      q = (qq - 1.0) * (r - 1.0) * (sq - 1.0);
+    }
+    if (p > 0.0) q = -q;
+    p = fabs(p);
+    if (2.0 * p < fmin(3.0 * xm * q - fabs(tol1 * q), fabs(s->e * q))) {
+      s->e = s->d;
+      s->d = p / q;
+    } else {
+      s->d = xm;
+      s->e = s->d;
+    }
+  } else {
+    s->d = xm;
+    s->e = s->d;
+  }
+  s->a = s->b;
+  s->fa = s->fb;
+  s->b += (fabs(s->d) > tol1) ? s->d : (xm > 0.0 ? tol1 : -tol1);
+  s->mu = s->b;
+}
+
+// enter Brent's method on the bracket [lo, hi] (f(lo) < 0 < f(hi))
+__device__ void mu_brent_start(MuState *s) {
+  s->phase = 3;
+  s->a = s->lo; s->fa = s->flo; s->b = s->hi; s->fb = s->fhi;
+  if (fabs(s->fa) < fabs(s->fb)) {
+    double t = s->a; s->a = s->b; s->b = t;
+    t = s->fa; s->fa = s->fb; s->fb = t;
+  }
+  s->c = s->a;
+  s->fc = s->fa;
+  s->d = s->b - s->a;
+  s->e = s->d;
+  mu_brent_next(s);
+}
+
+__global__ void mu_init_kernel(MuState *s, double mu0, double n_elec, double tol, int max_iter, int n_iw,
+                               int n_coarse, int *flag) {
+  if (threadIdx.x != 0) return;
+  s->n_elec = n_elec;
+  s->tol = tol;
+  s->tol_coarse = fmax(tol, 1e-9);
+  s->max_iter = max_iter;
+  s->cap_coarse = 60;
+  s->n_iw = n_iw;
+  s->n_coarse = n_coarse;
+  s->status = 0;
+  s->evals = 0;
+  s->mu_out = mu0;
+  s->stage = n_coarse > 0 ? 0 : 1;
+  if (n_coarse > 0) mu_solve_begin(s, mu0, 0.0, s->tol_coarse, s->cap_coarse, n_coarse);
+  else mu_solve_begin(s, mu0, 0.0, tol, max_iter, n_iw);
+  *flag = 0;
+}
+
+// after an evaluation at s->mu: record it and choose the next point
+__global__ void mu_control_kernel(MuState *s, const double *count, const int *flag,
+                                  cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0) return;
+  const double f = count[0] - s->n_elec;
+  ++s->evals;
+  if (*flag) {
+    s->status = 4;
+    s->stage = 2;
+  } else if (!isfinite(f)) {
+    s->status = 3;
+    s->stage = 2;
+  } else {
+    ++s->n;
+    if (s->n > 1) {
+      s->prev_mu = s->last_mu;
+      s->prev_f = s->last_f;
+      s->have_prev = 1;
+    }
+    s->last_mu = s->mu;
+    s->last_f = f;
+    if (fabs(f) <= s->tol_f) {
+      mu_solve_end(s, true);
+    } else if (s->phase == 0) {
+      // N(mu) increases with mu; with a slope hint the first probe is the Newton step
+      const double h = s->slope_hint;
+      s->step = (h > 0.0 && isfinite(h)) ? fmin(0.05, fmax(1e-12, fabs(f) / h)) : 0.05;
+      if (f < 0.0) {
+        s->lo = s->mu; s->flo = f; s->hi = s->mu + s->step; s->phase = 1; s->mu = s->hi;
+      } else {
+        s->hi = s->mu; s->fhi = f; s->lo = s->mu - s->step; s->phase = 2; s->mu = s->lo;
+      }
+      if (s->n >= s->cap) mu_solve_end(s, false);
+    } else if (s->phase == 1) {
+      s->fhi = f;
+      if (f > 0.0) {
+        mu_brent_start(s);
+      } else {
+        s->lo = s->hi; s->flo = f; s->step *= 2.0; s->hi += s->step; s->mu = s->hi;
+        if (s->n >= s->cap) mu_solve_end(s, false);
+      }
+    } else if (s->phase == 2) {
+      s->flo = f;
+      if (f < 0.0) {
+        mu_brent_start(s);
+      } else {
+        s->hi = s->lo; s->fhi = f; s->step *= 2.0; s->lo -= s->step; s->mu = s->lo;
+        if (s->n >= s->cap) mu_solve_end(s, false);
+      }
+    } else {
+      s->fb = f;
+      mu_brent_next(s);
+    }
+  }
+  cudaGraphSetConditional(loop, s->stage == 2 ? 0u : 1u);
 }
 
 // Eq. FockMatrix, F = h + J - K/2 with J_ij = sum_kl P_kl v_ijlk and
@@ -478,6 +691,70 @@ extern "C" gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const doub
   return launch_density(ctx, d_G_iw, coef, d_P, ctx->n_iw, ctx->d_pole_resum);
 }
 
+// The WHILE graph of the device-resident search for one set of buffers (kept
+// while the buffers stay the same): moments, pole coefficients, Dyson over the
+// largest frequency range (blocks past the evaluation's range return), density,
+// trace and the controller, captured on a private stream into the loop body.
+static gf2_status mu_search_graph(gf2_ctx *ctx, const double *S, const double *F, const double *Sig,
+                                  double *G, double *P) {
+  const void *key[5] = {S, F, Sig, G, P};
+  if (ctx->mu_graph_exec && std::equal(key, key + 5, ctx->mu_graph_key)) return GF2_OK;
+  if (ctx->mu_graph_exec) cudaGraphExecDestroy(ctx->mu_graph_exec);
+  if (ctx->mu_graph) cudaGraphDestroy(ctx->mu_graph);
+  ctx->mu_graph_exec = nullptr;
+  ctx->mu_graph = nullptr;
+  if (!ctx->d_mu_state) GF2_CK(ctx, cudaMalloc(&ctx->d_mu_state, sizeof(MuState)));
+  if (!ctx->capture_stream) GF2_CK(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  MuState *ms = static_cast<MuState *>(ctx->d_mu_state);
+  cudaGraph_t graph = nullptr;
+  GF2_CK(ctx, cudaGraphCreate(&graph, 0));
+  ctx->mu_graph = graph;
+  cudaGraphConditionalHandle loop;
+  GF2_CK(ctx, cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = loop;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  GF2_CK(ctx, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs = ctx->capture_stream;
+  const int N = ctx->N, N2 = N * N, n_iw = ctx->n_iw;
+  double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
+  GF2_CK(ctx, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  moments_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, 0.0, ctx->d_small, mom, ms);
+  pole_coef_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, GF2_TAIL_POLE, mom, coef);
+  const int per = (N * (N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
+  const double2 *sg = reinterpret_cast<const double2 *>(Sig);
+  double2 *gg = reinterpret_cast<double2 *>(G);
+  const double b = ctx->beta;
+  int *fl = ctx->d_err;
+  if (per <= 1) dyson_kernel<1, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 2) dyson_kernel<2, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 4) dyson_kernel<4, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 5) dyson_kernel<5, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 9) dyson_kernel<9, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 16) dyson_kernel<16, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else dyson_kernel<kDysonMaxPerThread, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  const int chunk = 256, nchunks = (n_iw + chunk - 1) / chunk;
+  density_partial_kernel<<<dim3((N2 + 127) / 128, nchunks), 128, 0, cs>>>(
+      N2, n_iw, chunk, reinterpret_cast<const double2 *>(G), ctx->d_red, ms);
+  density_final_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, nchunks, ctx->beta, ctx->d_red, coef,
+                                                          ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M,
+                                                          P, ms, ctx->d_pole_resum + 4);
+  trace_kernel<<<1, 256, 0, cs>>>(N, P, S, cnt);
+  mu_control_kernel<<<1, 32, 0, cs>>>(ms, cnt, fl, loop);
+  const cudaError_t launch_err = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  const cudaError_t end_err = cudaStreamEndCapture(cs, &captured);
+  if (launch_err != cudaSuccess) return gf2_cuda_fail(ctx, launch_err, "mu search graph: kernel capture");
+  if (end_err != cudaSuccess) return gf2_cuda_fail(ctx, end_err, "mu search graph: end of capture");
+  GF2_CK(ctx, cudaGraphInstantiate(&ctx->mu_graph_exec, graph, 0));
+  std::copy(key, key + 5, ctx->mu_graph_key);
+  return GF2_OK;
+}
+
 extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
                                     const double *d_Sigma_iw, const double *d_sig12, double n_elec,
                                     double tol, int max_iter, double *mu_inout, double *d_G_iw,
@@ -490,167 +767,26 @@ extern "C" gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const doubl
     return gf2_fail(ctx, GF2_ERR_ARG, "gf2_mu_search: bad tol, max_iter, mu or n_elec");
   gf2_status st = build_moment_basis(ctx, d_S, d_F, d_sig12);
   if (st != GF2_OK) return st;
-  double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
-  int evals = 0;
-  // f(mu) = N(mu) - n_elec from the lowest nf frequencies (tail sums over the same range)
-  auto count = [&](double mu, int nf, const double *resum, double *out) -> gf2_status {
-    gf2_status s;
-    if ((s = launch_moments(ctx, mu, mom)) != GF2_OK) return s;
-    if ((s = gf2_pole_coefficients(ctx, mom, coef)) != GF2_OK) return s;
-    if ((s = launch_dyson(ctx, mu, d_S, d_F, d_Sigma_iw, d_G_iw, nf)) != GF2_OK) return s;
-    if ((s = launch_density(ctx, d_G_iw, coef, d_P, nf, resum)) != GF2_OK) return s;
-    trace_kernel<<<1, 256, 0, ctx->stream>>>(ctx->N, d_P, d_S, cnt);
-    GF2_CK_LAUNCH(ctx, "trace_kernel");
-    GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, cnt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
-    ++evals;
-    int flag = 0;
-    memcpy(&flag, ctx->h_pinned + 1, sizeof(int));
-    if (flag) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: vanishing Dyson pivot");
-    *out = ctx->h_pinned[0] - n_elec;
-    if (!std::isfinite(*out)) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: non-finite count");
-    return GF2_OK;
-  };
-  // Root of f from mu0: bracket outward (first step from the slope hint when
-  // there is one, else 0.05; doubling), then Brent's method.  *found tells
-  // whether |f| <= tol was reached; *mu_out is the last point evaluated and
-  // *slope the secant slope of the last two points (0 if unknown).
-  struct Result {
-    double mu = 0.0, slope = 0.0;
-    bool found = false;
-  };
-  auto solve = [&](double mu0, double slope_hint, double tol_f, int cap, int nf, const double *resum,
-                   int *used, Result *res) -> gf2_status {
-    gf2_status s;
-    int n = 0;
-    double last_mu = mu0, last_f = 0.0, prev_mu = 0.0, prev_f = 0.0;
-    bool have_prev = false;
-    auto eval = [&](double mu, double *f) -> gf2_status {
-      gf2_status e = count(mu, nf, resum, f);
-      if (e != GF2_OK) return e;
-      ++n;
-      if (n > 1) {
-        prev_mu = last_mu;
-        prev_f = last_f;
-        have_prev = true;
-      }
-      last_mu = mu;
-      last_f = *f;
-      return GF2_OK;
-    };
-    auto finish = [&](bool found) {
-      res->mu = last_mu;
-      res->found = found;
-      res->slope = (have_prev && last_mu != prev_mu) ? (last_f - prev_f) / (last_mu - prev_mu) : 0.0;
-      *used = n;
-      return GF2_OK;
-    };
-    double f0;
-    if ((s = eval(mu0, &f0)) != GF2_OK) return s;
-    if (fabs(f0) <= tol_f) return finish(true);
-    // N(mu) increases with mu; with a slope hint the first probe is the Newton
-    // step (it usually lands within tol; if it falls short the step doubles)
-    double step = (slope_hint > 0.0 && std::isfinite(slope_hint)) ? std::min(0.05, std::max(1e-12, fabs(f0) / slope_hint))
-                                                                    : 0.05;
-    double lo, hi, flo, fhi;
-    if (f0 < 0.0) {
-      lo = mu0; flo = f0; hi = mu0 + step;
-      for (;;) {
-        if (n >= cap) return finish(false);
-        if ((s = eval(hi, &fhi)) != GF2_OK) return s;
-        if (fabs(fhi) <= tol_f) return finish(true);
-        if (fhi > 0.0) break;
-        lo = hi; flo = fhi; step *= 2.0; hi += step;
-      }
-    } else {
-      hi = mu0; fhi = f0; lo = mu0 - step;
-      for (;;) {
-        if (n >= cap) return finish(false);
-        if ((s = eval(lo, &flo)) != GF2_OK) return s;
-        if (fabs(flo) <= tol_f) return finish(true);
-        if (flo < 0.0) break;
-        hi = lo; fhi = flo; step *= 2.0; lo -= step;
-      }
-    }
-    // Brent's method on the bracket: inverse quadratic interpolation or secant
-    // steps, falling back to bisection whenever they would not shrink it enough
-    double a = lo, fa = flo, b = hi, fb = fhi;
-    if (fabs(fa) < fabs(fb)) {
-      std::swap(a, b);
-      std::swap(fa, fb);
-    }
-    double c = a, fc = fa, d = b - a, e = d;
-    while (n < cap) {
-      if ((fb > 0.0) == (fc > 0.0)) {
-        c = a;
-        fc = fa;
-        d = e = b - a;
-      }
-      if (fabs(fc) < fabs(fb)) {
-        a = b; b = c; c = a;
-        fa = fb; fb = fc; fc = fa;
-      }
-      const double tol1 = 2.0 * 2.2e-16 * fabs(b) + 1e-16;
-      const double xm = 0.5 * (c - b);
-      if (fabs(xm) <= tol1) break;  // bracket collapsed without reaching tol
-      if (fabs(e) >= tol1 && fabs(fa) > fabs(fb)) {
-        const double sq = fb / fa;
-        double p, q;
-        if (a == c) {
-          p = 2.0 * xm * sq;
-          q = 1.0 - sq;
-        } else {
-          const double qq = fa / fc, r = fb / fc;
-          p = sq * (2.0 * xm * qq * (qq - r) - (b - a) * (r - 1.0));
-          q = (qq - 1.0) * (r - 1.0) * (sq - 1.0);
-        }
-        if (p > 0.0) q = -q;
-        p = fabs(p);
-        if (2.0 * p < std::min(3.0 * xm * q - fabs(tol1 * q), fabs(e * q))) {
-          e = d;
-          d = p / q;
-        } else {
-          d = xm;
-          e = d;
-        }
-      } else {
-        d = xm;
-        e = d;
-      }
-      a = b;
-      fa = fb;
-      b += (fabs(d) > tol1) ? d : (xm > 0.0 ? tol1 : -tol1);
-      if ((s = eval(b, &fb)) != GF2_OK) return s;
-      if (fabs(fb) <= tol_f) return finish(true);
-    }
-    return finish(false);
-  };
-
-  // Coarse stage: the count over the lowest n_iw/8 frequencies (plus the
-  // analytic tail) differs from the full count by far less than the bracketing
-  // scale, so it locates mu and the local slope at an eighth of the cost.  The
-  // full-frequency stage then starts there with a slope-sized first step and
-  // decides convergence on the full count alone.
-  double mu_start = *mu_inout, slope = 0.0;
-  if (ctx->n_coarse > 0) {
-    Result rc;
-    int used = 0;
-    if ((st = solve(mu_start, 0.0, std::max(tol, 1e-9), 60, ctx->n_coarse, ctx->d_pole_resum + 4, &used, &rc)) !=
-        GF2_OK)
-      return st;
-    if (rc.found && std::isfinite(rc.mu)) {
-      mu_start = rc.mu;
-      slope = rc.slope;
-    }
-  }
-  Result rf;
-  int used = 0;
-  st = solve(mu_start, slope, tol, max_iter, ctx->n_iw, ctx->d_pole_resum, &used, &rf);
+  if ((st = mu_search_graph(ctx, d_S, d_F, d_Sigma_iw, d_G_iw, d_P)) != GF2_OK) return st;
+  MuState *ms = static_cast<MuState *>(ctx->d_mu_state);
+  mu_init_kernel<<<1, 32, 0, ctx->stream>>>(ms, *mu_inout, n_elec, tol, max_iter, ctx->n_iw, ctx->n_coarse,
+                                           ctx->d_err);
+  GF2_CK_LAUNCH(ctx, "mu_init_kernel");
+  GF2_PROF(ctx, GF2_K_DYSON, GF2_CK(ctx, cudaGraphLaunch(ctx->mu_graph_exec, ctx->stream)));
+  // the one host synchronization of the search: its result
+  static_assert(sizeof(MuState) >= 3 * sizeof(double), "state");
+  GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, &ms->mu_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  GF2_CK(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, &ms->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  GF2_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  int st_ev[2];
+  std::memcpy(st_ev, ctx->h_pinned + 1, sizeof(st_ev));
+  const int status = st_ev[0], evals = st_ev[1];
+  ctx->launches += 7LL * evals;  // the graph's kernels: seven per count evaluation
   if (n_eval) *n_eval = evals;
-  if (st != GF2_OK) return st;
-  *mu_inout = rf.mu;
-  if (!rf.found) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: tolerance not reached");
+  if (status == 4) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: vanishing Dyson pivot");
+  if (status == 3) return gf2_fail(ctx, GF2_ERR_NONFINITE, "gf2_mu_search: non-finite count");
+  *mu_inout = ctx->h_pinned[0];
+  if (status != 1) return gf2_fail(ctx, GF2_ERR_NOT_CONVERGED, "gf2_mu_search: tolerance not reached");
   return GF2_OK;
 }
 

@@ -55,6 +55,10 @@ void prof_drain(gf2_ctx *c) {
 }
 
 void free_all(gf2_ctx *c) {
+  if (c->mu_graph_exec) cudaGraphExecDestroy(c->mu_graph_exec);
+  if (c->mu_graph) cudaGraphDestroy(c->mu_graph);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->d_mu_state) cudaFree(c->d_mu_state);
   for (auto &r : c->prof_recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -81,6 +81,14 @@ struct gf2_ctx {
   bool defer_error_check = false; // set while a batch records this context into a CUDA graph:
                                   // the split path then skips its closing read of d_err
 
+  // device-resident chemical-potential search: its state and the CUDA graph
+  // (a WHILE conditional node around one count evaluation) that runs it
+  void *d_mu_state = nullptr;
+  cudaGraph_t mu_graph = nullptr;
+  cudaGraphExec_t mu_graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  const void *mu_graph_key[5] = {};
+
   // small scratch
   double *d_small = nullptr;      // Sinv, basis(7), coef(4), misc: 16 N^2
   double *d_red = nullptr;        // reduction partials

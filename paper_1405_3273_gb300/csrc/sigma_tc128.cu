@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(320, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
+  // a contiguous block of units per CTA (balanced to within one unit)
   const int u_begin = (int)((long long)blockIdx.x * n_units / gridDim.x);
   const int u_end = (int)((long long)(blockIdx.x + 1) * n_units / gridDim.x);
 
@@ -550,6 +551,7 @@ __global__ void __launch_bounds__(320, 1)
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   volatile int *abort = &s_abort;
+  // a contiguous block of units per CTA (balanced to within one unit)
   const int u_begin = (int)((long long)blockIdx.x * n_units / gridDim.x);
   const int u_end = (int)((long long)(blockIdx.x + 1) * n_units / gridDim.x);
 

@@ -183,6 +183,35 @@ gf2_status gf2_mu_search(gf2_ctx *ctx, const double *d_S, const double *d_F,
                          double tol, int max_iter, double *mu_inout, double *d_G_iw,
                          double *d_P, int *n_eval);
 
+/* Steps 2.a-2.b, the inner self-consistency loop at fixed Sigma: alternate
+ * the mu search (as gf2_mu_search, tolerance mu_tol, at most 100 full
+ * evaluations) and the Fock rebuild F_out = Fock(P) (as gf2_fock) until the
+ * residual R = F_out - F has Frobenius norm below tol; then F = F_out and a
+ * last mu search gives G(i w), P and mu at that F.  The next F while
+ * |R| > diis_from (or diis = 0) is the damped step F + mix R, which also
+ * empties the history; for |R| <= diis_from it is the Pulay (DIIS)
+ * combination sum_k c_k F_out_k of the last diis (<= 8) rebuilt matrices,
+ * c minimising |sum_k c_k R_k| under sum_k c_k = 1 (the bordered Gram system
+ * solved by Gaussian elimination with partial pivoting; a singular system
+ * drops the oldest entry).  The supplement damps P instead; the Fock-matrix
+ * schedule is this library's convergence aid.
+ * The whole loop runs as one CUDA graph whose decisions are taken on the
+ * device (a WHILE node around one iteration, the mu search's WHILE node
+ * nested in it); the host reads one block of scalars at the end.
+ * d_S, d_h [N][N] in; d_F [N][N] in: the start, out: the converged F;
+ * d_Sigma_iw [n_iw][N][N] c128 and d_sig12 [2][N][N] in (both may be NULL for
+ * Sigma = 0); *mu_inout in: the first search's start, out: mu; d_G_iw, d_P
+ * out (must not alias the inputs).  *n_iter = Fock rebuilds, *n_mu_eval =
+ * Dyson evaluations of all searches (either may be NULL).  Errors:
+ * GF2_ERR_NOT_CONVERGED after max_iter rebuilds or when a mu search misses
+ * its tolerance (d_F then holds the last iterate), GF2_ERR_NONFINITE for a
+ * vanishing Dyson pivot or a non-finite count or residual.  Synchronizes. */
+gf2_status gf2_inner_loop(gf2_ctx *ctx, const double *d_S, const double *d_h, double *d_F,
+                          const double *d_Sigma_iw, const double *d_sig12, double n_elec,
+                          double *mu_inout, double *d_G_iw, double *d_P, double tol, int max_iter,
+                          double mu_tol, int diis, double mix, double diis_from, int *n_iter,
+                          int *n_mu_eval);
+
 /* Eq. FockMatrix: F_ij = h_ij + sum_kl P_kl (v_ijlk - v_iklj / 2), with the
  * integrals given to gf2_set_integrals (no index symmetry of v is assumed).
  * d_h, d_P [N][N] in, d_F [N][N] out.  d_F may be d_h (F replaces h in

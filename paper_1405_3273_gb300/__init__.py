@@ -48,6 +48,8 @@ _SIGS = {
     "gf2_dyson": [_P, _D, _P, _P, _P, _P],
     "gf2_density": [_P, _P, _P, _P],
     "gf2_mu_search": [_P, _P, _P, _P, _P, _D, _D, _I, ctypes.POINTER(_D), _P, _P, ctypes.POINTER(_I)],
+    "gf2_inner_loop": [_P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(_D), _P, _P, _D, _I, _D, _I, _D, _D,
+                       ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "gf2_fock": [_P, _P, _P, _P],
     "gf2_energy": [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "gf2_combine": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_P), ctypes.c_longlong, _P],
@@ -181,6 +183,18 @@ def gf2_mu_search(ctx, S, F, Sigma_iw, sig12, n_elec, mu0, G_iw, P, tol=1e-10, m
                                ctypes.byref(mu), _ptr(G_iw, _C128), _ptr(P, _F64),
                                ctypes.byref(nev)), ctx)
     return mu.value, nev.value
+
+
+def gf2_inner_loop(ctx, S, h, F, Sigma_iw, sig12, n_elec, mu0, G_iw, P, tol=1e-8, max_iter=300,
+                   mu_tol=1e-10, diis=8, mix=0.5, diis_from=1e-3):
+    """Device-resident inner loop; F is updated in place.  Returns (mu, iterations, mu evaluations)."""
+    mu = ctypes.c_double(float(mu0))
+    nit, nev = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().gf2_inner_loop(ctx, _ptr(S, _F64), _ptr(h, _F64), _ptr(F, _F64), _ptr(Sigma_iw, _C128),
+                                _ptr(sig12, _F64), float(n_elec), ctypes.byref(mu), _ptr(G_iw, _C128),
+                                _ptr(P, _F64), float(tol), int(max_iter), float(mu_tol), int(diis), float(mix),
+                                float(diis_from), ctypes.byref(nit), ctypes.byref(nev)), ctx)
+    return mu.value, nit.value, nev.value
 
 
 def gf2_fock(ctx, h, P, F):

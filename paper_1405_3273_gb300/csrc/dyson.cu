@@ -26,23 +26,7 @@ enum { SL_SINV = GF2_SL_SINV, SL_A1 = GF2_SL_A1, SL_A2 = GF2_SL_A2, SL_A3 = GF2_
        SL_B1 = GF2_SL_B1, SL_B2 = GF2_SL_B2, SL_B3 = GF2_SL_B3, SL_T1 = GF2_SL_T1, SL_TMP = GF2_SL_TMP,
        SL_MOM = GF2_SL_MOM, SL_COEF = GF2_SL_COEF, SL_MISC = GF2_SL_MISC };
 
-// State of the device-resident chemical-potential search (step 2.a): the point
-// to evaluate next and the bracket / Brent variables, updated by one thread
-// after every count evaluation (see mu_control_kernel).
-struct MuState {
-  double n_elec, tol, tol_coarse;   // inputs
-  int max_iter, cap_coarse, n_iw, n_coarse;
-  double mu;                        // next point to evaluate
-  int nf;                           // frequencies of that evaluation
-  int stage;                        // 0 coarse, 1 full, 2 done
-  int status;                       // 0 running, 1 found, 2 not converged, 3 non-finite count, 4 vanishing pivot
-  int evals;
-  double mu_out;
-  int phase;                        // 0 first point, 1 bracketing upward, 2 downward, 3 Brent
-  int n, cap, have_prev;
-  double slope_hint, tol_f, step, lo, hi, flo, fhi, a, b, c, fa, fb, fc, d, e;
-  double last_mu, last_f, prev_mu, prev_f;
-};
+using MuState = gf2_mu_state;
 
 __global__ void pole_coef_kernel(int N2, double a, const double *mom, double *coef) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,9 +318,7 @@ __device__ void mu_brent_start(MuState *s) {
   mu_brent_next(s);
 }
 
-__global__ void mu_init_kernel(MuState *s, double mu0, double n_elec, double tol, int max_iter, int n_iw,
-                               int n_coarse, int *flag) {
-  if (threadIdx.x != 0) return;
+__device__ void mu_init(MuState *s, double mu0, double n_elec, double tol, int max_iter, int n_iw, int n_coarse) {
   s->n_elec = n_elec;
   s->tol = tol;
   s->tol_coarse = fmax(tol, 1e-9);
@@ -350,7 +332,25 @@ __global__ void mu_init_kernel(MuState *s, double mu0, double n_elec, double tol
   s->stage = n_coarse > 0 ? 0 : 1;
   if (n_coarse > 0) mu_solve_begin(s, mu0, 0.0, s->tol_coarse, s->cap_coarse, n_coarse);
   else mu_solve_begin(s, mu0, 0.0, tol, max_iter, n_iw);
+}
+
+__global__ void mu_init_kernel(MuState *s, double mu0, double n_elec, double tol, int max_iter, int n_iw,
+                               int n_coarse, int *flag) {
+  if (threadIdx.x != 0) return;
+  mu_init(s, mu0, n_elec, tol, max_iter, n_iw, n_coarse);
   *flag = 0;
+}
+
+// the same inside a graph: the start value and the search parameters come from
+// device memory, prm = {mu0, n_elec, tol, max_iter}, and the loop that follows
+// is armed (a WHILE node nested in another loop's body keeps the value its
+// last run left)
+__global__ void mu_start_kernel(MuState *s, const double *prm, int n_iw, int n_coarse, int *flag,
+                                cudaGraphConditionalHandle loop) {
+  if (threadIdx.x != 0) return;
+  mu_init(s, prm[0], prm[1], prm[2], (int)prm[3], n_iw, n_coarse);
+  *flag = 0;
+  cudaGraphSetConditional(loop, 1u);
 }
 
 // after an evaluation at s->mu: record it and choose the next point
@@ -586,12 +586,14 @@ Dgemm square_gemm(int N, const double *A, const double *B, double *C, double alp
   return g;
 }
 
-// moment basis A0..A3, B1..B3 into the small slots
-gf2_status build_moment_basis(gf2_ctx *ctx, const double *S, const double *F, const double *sig12) {
+// moment basis A0..A3, B1..B3 into the small slots (S^-1 kept from the last
+// call when invert_S is false)
+gf2_status build_moment_basis(gf2_ctx *ctx, const double *S, const double *F, const double *sig12,
+                              bool invert_S = true) {
   const int N = ctx->N;
   const size_t N2 = (size_t)N * N;
   gf2_status st;
-  if ((st = gf2_inverse_spd(ctx, S, slot(ctx, SL_SINV))) != GF2_OK) return st;
+  if (invert_S && (st = gf2_inverse_spd(ctx, S, slot(ctx, SL_SINV))) != GF2_OK) return st;
   double *Sinv = slot(ctx, SL_SINV), *T1 = slot(ctx, SL_T1), *tmp = slot(ctx, SL_TMP);
   if ((st = gf2_dgemm(ctx, square_gemm(N, Sinv, F, T1, 1.0, 0.0))) != GF2_OK) return st;
   if ((st = gf2_dgemm(ctx, square_gemm(N, T1, Sinv, slot(ctx, SL_A1), 1.0, 0.0))) != GF2_OK) return st;
@@ -691,6 +693,36 @@ extern "C" gf2_status gf2_density(gf2_ctx *ctx, const double *d_G_iw, const doub
   return launch_density(ctx, d_G_iw, coef, d_P, ctx->n_iw, ctx->d_pole_resum);
 }
 
+// One count evaluation at the state's mu, then the controller: the body of the
+// search's WHILE loop (seven kernels), launched on the capturing stream cs.
+static void launch_mu_body(gf2_ctx *ctx, cudaStream_t cs, const double *S, const double *F, const double *Sig,
+                    double *G, double *P, MuState *ms, cudaGraphConditionalHandle loop) {
+  const int N = ctx->N, N2 = N * N, n_iw = ctx->n_iw;
+  double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
+  moments_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, 0.0, ctx->d_small, mom, ms);
+  pole_coef_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, GF2_TAIL_POLE, mom, coef);
+  const int per = (N * (N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
+  const double2 *sg = reinterpret_cast<const double2 *>(Sig);
+  double2 *gg = reinterpret_cast<double2 *>(G);
+  const double b = ctx->beta;
+  int *fl = ctx->d_err;
+  if (per <= 1) dyson_kernel<1, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 2) dyson_kernel<2, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 4) dyson_kernel<4, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 5) dyson_kernel<5, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 9) dyson_kernel<9, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else if (per <= 16) dyson_kernel<16, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  else dyson_kernel<kDysonMaxPerThread, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
+  const int chunk = 256, nchunks = (n_iw + chunk - 1) / chunk;
+  density_partial_kernel<<<dim3((N2 + 127) / 128, nchunks), 128, 0, cs>>>(
+      N2, n_iw, chunk, reinterpret_cast<const double2 *>(G), ctx->d_red, ms);
+  density_final_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, nchunks, ctx->beta, ctx->d_red, coef,
+                                                          ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M,
+                                                          P, ms, ctx->d_pole_resum + 4);
+  trace_kernel<<<1, 256, 0, cs>>>(N, P, S, cnt);
+  mu_control_kernel<<<1, 32, 0, cs>>>(ms, cnt, fl, loop);
+}
+
 // The WHILE graph of the device-resident search for one set of buffers (kept
 // while the buffers stay the same): moments, pole coefficients, Dyson over the
 // largest frequency range (blocks past the evaluation's range return), density,
@@ -720,31 +752,8 @@ static gf2_status mu_search_graph(gf2_ctx *ctx, const double *S, const double *F
   GF2_CK(ctx, cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
   cudaStream_t cs = ctx->capture_stream;
-  const int N = ctx->N, N2 = N * N, n_iw = ctx->n_iw;
-  double *mom = slot(ctx, SL_MOM), *coef = slot(ctx, SL_COEF), *cnt = slot(ctx, SL_MISC);
   GF2_CK(ctx, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  moments_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, 0.0, ctx->d_small, mom, ms);
-  pole_coef_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, GF2_TAIL_POLE, mom, coef);
-  const int per = (N * (N + 1) / 2 + kDysonThreads - 1) / kDysonThreads;
-  const double2 *sg = reinterpret_cast<const double2 *>(Sig);
-  double2 *gg = reinterpret_cast<double2 *>(G);
-  const double b = ctx->beta;
-  int *fl = ctx->d_err;
-  if (per <= 1) dyson_kernel<1, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else if (per <= 2) dyson_kernel<2, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else if (per <= 4) dyson_kernel<4, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else if (per <= 5) dyson_kernel<5, 2><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else if (per <= 9) dyson_kernel<9, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else if (per <= 16) dyson_kernel<16, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  else dyson_kernel<kDysonMaxPerThread, 1><<<n_iw, kDysonThreads, 0, cs>>>(N, b, 0.0, S, F, sg, gg, fl, ms);
-  const int chunk = 256, nchunks = (n_iw + chunk - 1) / chunk;
-  density_partial_kernel<<<dim3((N2 + 127) / 128, nchunks), 128, 0, cs>>>(
-      N2, n_iw, chunk, reinterpret_cast<const double2 *>(G), ctx->d_red, ms);
-  density_final_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, nchunks, ctx->beta, ctx->d_red, coef,
-                                                          ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M,
-                                                          P, ms, ctx->d_pole_resum + 4);
-  trace_kernel<<<1, 256, 0, cs>>>(N, P, S, cnt);
-  mu_control_kernel<<<1, 32, 0, cs>>>(ms, cnt, fl, loop);
+  launch_mu_body(ctx, cs, S, F, Sig, G, P, ms, loop);
   const cudaError_t launch_err = cudaGetLastError();
   cudaGraph_t captured = nullptr;
   const cudaError_t end_err = cudaStreamEndCapture(cs, &captured);
@@ -752,6 +761,46 @@ static gf2_status mu_search_graph(gf2_ctx *ctx, const double *S, const double *F
   if (end_err != cudaSuccess) return gf2_cuda_fail(ctx, end_err, "mu search graph: end of capture");
   GF2_CK(ctx, cudaGraphInstantiate(&ctx->mu_graph_exec, graph, 0));
   std::copy(key, key + 5, ctx->mu_graph_key);
+  return GF2_OK;
+}
+
+gf2_status gf2_build_moment_basis(gf2_ctx *ctx, const double *S, const double *F, const double *sig12,
+                                  bool invert_S) {
+  return build_moment_basis(ctx, S, F, sig12, invert_S);
+}
+
+gf2_status gf2_capture_mu_search(gf2_ctx *ctx, cudaStream_t parent, cudaStream_t body_stream, const double *S,
+                                 const double *F, const double *Sig, double *G, double *P, const double *prm) {
+  if (!ctx->d_mu_state) GF2_CK(ctx, cudaMalloc(&ctx->d_mu_state, sizeof(MuState)));
+  MuState *ms = static_cast<MuState *>(ctx->d_mu_state);
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  GF2_CK(ctx, cudaStreamGetCaptureInfo(parent, &cst, nullptr, &g));
+  if (cst != cudaStreamCaptureStatusActive || !g)
+    return gf2_fail(ctx, GF2_ERR_ARG, "gf2_capture_mu_search: parent stream is not capturing");
+  cudaGraphConditionalHandle loop;
+  GF2_CK(ctx, cudaGraphConditionalHandleCreate(&loop, g, 0, 0));  // armed by mu_start_kernel
+  mu_start_kernel<<<1, 32, 0, parent>>>(ms, prm, ctx->n_iw, ctx->n_coarse, ctx->d_err, loop);
+  GF2_CK(ctx, cudaGetLastError());
+  const cudaGraphNode_t *deps = nullptr;
+  size_t n_deps = 0;
+  GF2_CK(ctx, cudaStreamGetCaptureInfo(parent, &cst, nullptr, &g, &deps, nullptr, &n_deps));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = loop;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  GF2_CK(ctx, cudaGraphAddNode(&node, g, deps, nullptr, n_deps, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  GF2_CK(ctx, cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_mu_body(ctx, body_stream, S, F, Sig, G, P, ms, loop);
+  const cudaError_t launch_err = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  const cudaError_t end_err = cudaStreamEndCapture(body_stream, &captured);
+  if (launch_err != cudaSuccess) return gf2_cuda_fail(ctx, launch_err, "nested mu search: kernel capture");
+  if (end_err != cudaSuccess) return gf2_cuda_fail(ctx, end_err, "nested mu search: end of capture");
+  GF2_CK(ctx, cudaStreamUpdateCaptureDependencies(parent, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
   return GF2_OK;
 }
 

@@ -39,7 +39,8 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 const char *kKernelNames[GF2_K_COUNT] = {"sigma_sandwich", "sigma_xform", "sigma_contract", "sigma_split_g",
                                          "dgemm_fp64", "dyson_inverse", "density_reduce", "fft_iw_to_tau",
-                                         "fft_tau_to_iw", "fock_build", "energy_reduce", "small"};
+                                         "fft_tau_to_iw", "fock_build", "energy_reduce", "small",
+                                         "inner_loop_graph"};
 
 void prof_drain(gf2_ctx *c) {
   for (auto &r : c->prof_recs) {
@@ -58,6 +59,11 @@ void free_all(gf2_ctx *c) {
   if (c->mu_graph_exec) cudaGraphExecDestroy(c->mu_graph_exec);
   if (c->mu_graph) cudaGraphDestroy(c->mu_graph);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->inner_graph_exec) cudaGraphExecDestroy(c->inner_graph_exec);
+  if (c->inner_graph) cudaGraphDestroy(c->inner_graph);
+  if (c->capture_stream2) cudaStreamDestroy(c->capture_stream2);
+  if (c->capture_stream3) cudaStreamDestroy(c->capture_stream3);
+  if (c->d_inner_ws) cudaFree(c->d_inner_ws);
   if (c->d_mu_state) cudaFree(c->d_mu_state);
   for (auto &r : c->prof_recs) {
     cudaEventDestroy(r.a);

@@ -22,7 +22,25 @@ enum {
 // kernels timed by the optional per-launch profiler (gf2_profile)
 enum gf2_kernel_id {
   GF2_K_SANDWICH = 0, GF2_K_XFORM, GF2_K_CONTRACT, GF2_K_SPLIT, GF2_K_DGEMM, GF2_K_DYSON,
-  GF2_K_DENSITY, GF2_K_IW2TAU, GF2_K_TAU2IW, GF2_K_FOCK, GF2_K_ENERGY, GF2_K_SMALL, GF2_K_COUNT
+  GF2_K_DENSITY, GF2_K_IW2TAU, GF2_K_TAU2IW, GF2_K_FOCK, GF2_K_ENERGY, GF2_K_SMALL, GF2_K_INNER, GF2_K_COUNT
+};
+
+// State of the device-resident chemical-potential search (step 2.a): the point
+// to evaluate next and the bracket / Brent variables, updated by one thread
+// after every count evaluation (mu_control_kernel in dyson.cu).
+struct gf2_mu_state {
+  double n_elec, tol, tol_coarse;   // inputs
+  int max_iter, cap_coarse, n_iw, n_coarse;
+  double mu;                        // next point to evaluate
+  int nf;                           // frequencies of that evaluation
+  int stage;                        // 0 coarse, 1 full, 2 done
+  int status;                       // 0 running, 1 found, 2 not converged, 3 non-finite count, 4 vanishing pivot
+  int evals;
+  double mu_out;
+  int phase;                        // 0 first point, 1 bracketing upward, 2 downward, 3 Brent
+  int n, cap, have_prev;
+  double slope_hint, tol_f, step, lo, hi, flo, fhi, a, b, c, fa, fb, fc, d, e;
+  double last_mu, last_f, prev_mu, prev_f;
 };
 
 struct gf2_prof_rec {
@@ -88,6 +106,15 @@ struct gf2_ctx {
   cudaGraphExec_t mu_graph_exec = nullptr;
   cudaStream_t capture_stream = nullptr;
   const void *mu_graph_key[5] = {};
+
+  // device-resident inner loop (steps 2.a-2.b, inner.cu): its state, residual
+  // history and graph (a WHILE node whose body nests the mu search's)
+  void *d_inner_ws = nullptr;
+  cudaGraph_t inner_graph = nullptr;
+  cudaGraphExec_t inner_graph_exec = nullptr;
+  cudaStream_t capture_stream2 = nullptr, capture_stream3 = nullptr;
+  const void *inner_graph_key[7] = {};
+  long long inner_kernels_per_iter = 0, inner_kernels_tail = 0;
 
   // small scratch
   double *d_small = nullptr;      // Sinv, basis(7), coef(4), misc: 16 N^2
@@ -164,6 +191,17 @@ void gf2_tc128_release(gf2_ctx *ctx);
 gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int count, double **d_Gorth);
 gf2_status gf2_orth_transform_v(gf2_ctx *ctx, double *d_vorth);
 gf2_status gf2_symmetrize(gf2_ctx *ctx, double *d_X, int count);
+// the moment basis of Eq. GF's tail (A1..A3 from S^-1 F, B1..B3 from Sig1, Sig2)
+// into the small slots; S^-1 is recomputed only when invert_S is set
+gf2_status gf2_build_moment_basis(gf2_ctx *ctx, const double *S, const double *F, const double *sig12,
+                                  bool invert_S);
+// Appends to the graph being captured on `parent` one whole mu search (step
+// 2.a): its start, with prm = {mu0, n_elec, tol, max_iter} read from device
+// memory when it runs, and a WHILE node around one count evaluation whose body
+// is captured on body_stream.  The result is in ctx->d_mu_state.  Seven kernels
+// per evaluation plus the start.
+gf2_status gf2_capture_mu_search(gf2_ctx *ctx, cudaStream_t parent, cudaStream_t body_stream, const double *S,
+                                 const double *F, const double *Sig, double *G, double *P, const double *prm);
 
 // ---- small device helpers ----
 __host__ __device__ inline double2 cmul(double2 a, double2 b) {

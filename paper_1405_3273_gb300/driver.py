@@ -13,8 +13,8 @@ import torch
 import numpy as np
 
 from . import (GF2_PREC_BF16X3, GF2_PREC_FP64, Context, gf2_combine, gf2_energy, gf2_fft_iw_to_tau,
-               gf2_fft_tau_to_iw, gf2_fock, gf2_gram, gf2_mu_search, gf2_set_integrals, gf2_set_overlap, gf2_sigma_tau,
-               gf2_tail_moments)
+               gf2_fft_tau_to_iw, gf2_fock, gf2_gram, gf2_inner_loop, gf2_mu_search, gf2_set_integrals,
+               gf2_set_overlap, gf2_sigma_tau, gf2_tail_moments)
 
 
 @dataclass
@@ -58,6 +58,8 @@ class GF2Run:
     moments: torch.Tensor = None
     energies: list = field(default_factory=list)
     mu_evals: list = field(default_factory=list)
+    inner_iters: list = field(default_factory=list)
+    device_inner: bool = True
 
 
 def start(sys, prec=GF2_PREC_FP64):
@@ -90,15 +92,26 @@ def _diis_coefficients(gram):
     return np.linalg.lstsq(B, rhs, rcond=None)[0][:m]
 
 
-def inner_loop(run, tol=1e-8, max_iter=300, mu_tol=1e-10, diis=8, mix=0.5, diis_from=1e-3):
+def inner_loop(run, tol=1e-8, max_iter=300, mu_tol=1e-10, diis=8, mix=0.5, diis_from=1e-3, device=None):
     """Steps 2.a-2.b: mu search and Fock rebuild until the Fock residual
     R = F(P(F)) - F has Frobenius norm below ``tol``.  Far from the fixed point
     (|R| > ``diis_from``) the next F is the damped step F + mix R; closer in it is
     the Pulay (DIIS) extrapolation of the last ``diis`` rebuilt matrices.  (From
     the HF state of a correlated lattice the fixed point can sit 20 mEh away in
-    mu, where DIIS alone wanders.)  G, P and mu are re-evaluated at the converged F."""
+    mu, where DIIS alone wanders.)  G, P and mu are re-evaluated at the converged F.
+
+    ``device`` (default: ``run.device_inner``) runs the whole loop as one
+    device-resident graph (gf2_inner_loop); otherwise the host sequences the
+    same steps call by call (one synchronization per mu search and Gram matrix)."""
     s = run.sys
     h = run.ctx.handle
+    if run.device_inner if device is None else device:
+        run.mu, nit, nev = gf2_inner_loop(h, s.S, s.h, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,
+                                          run.G_iw, run.P, tol=tol, max_iter=max_iter, mu_tol=mu_tol, diis=diis,
+                                          mix=mix, diis_from=diis_from)
+        run.mu_evals.append(nev)
+        run.inner_iters.append(nit)
+        return
     hist_F, hist_R = [], []
     for _ in range(max_iter):
         run.mu, nev = gf2_mu_search(h, s.S, run.F, run.Sigma_iw, run.sig12, s.n_elec, run.mu,

@@ -26,7 +26,7 @@ def library():
 def test_header_declares_the_hot_path_calls():
     names = declared_functions()
     for required in ["gf2_sigma_tau", "gf2_fft_tau_to_iw", "gf2_fft_iw_to_tau", "gf2_dyson",
-                     "gf2_mu_search", "gf2_energy", "gf2_create", "gf2_destroy"]:
+                     "gf2_mu_search", "gf2_inner_loop", "gf2_fock", "gf2_energy", "gf2_create", "gf2_destroy"]:
         assert required in names
 
 

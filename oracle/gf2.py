@@ -23,7 +23,8 @@ from . import dyson as dy
 from . import energy as en
 from .fock import fock
 from .sigma import sigma_tau
-from .transforms import iw_to_tau, sigma_expansion, tail_moments, tau_to_iw
+from .transforms import (iw_to_tau, sigma_expansion, sigma_expansion_grid, tail_moments, tau_to_iw,
+                         tau_to_iw_grid)
 
 
 @dataclass
@@ -106,29 +107,42 @@ def energy(system, state, beta):
     return system.e_nuc + e1 + e2, e1, e2
 
 
-def self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn=None):
-    """G(i w) -> G(tau) -> Sigma(tau) -> Sigma(i w) for the current state."""
+def self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn=None, grid=None):
+    """G(i w) -> G(tau) -> Sigma(tau) for the current state, on the uniform grid
+    of n_tau points or on grid = (M, index) (``grids.power_mesh``)."""
     mom = tail_moments(system.S, state.F, state.mu, state.sig1, state.sig2)
-    G_tau = iw_to_tau(state.G_iw, mom, beta, n_tau)
+    if grid is None:
+        G_tau = iw_to_tau(state.G_iw, mom, beta, n_tau)
+    else:
+        G_tau = iw_to_tau(state.G_iw, mom, beta, grid[0] + 1, taus=grid[1])
     Sig_tau = (sigma_fn or sigma_tau)(G_tau, system.eri)
     return G_tau, Sig_tau
 
 
+def sigma_to_iw(Sig_tau, beta, n_iw, grid=None):
+    """Sigma(i w), Sig1, Sig2 from Sigma(tau) on the uniform grid or on grid = (M, index)."""
+    if grid is None:
+        return (tau_to_iw(Sig_tau, beta, n_iw),) + tuple(sigma_expansion(Sig_tau, beta))
+    M, index = grid
+    return (tau_to_iw_grid(Sig_tau, beta, M, index, n_iw),) + tuple(sigma_expansion_grid(Sig_tau, beta, M, index))
+
+
 def run(system, F_start, beta, n_tau, n_iw, max_outer=30, e_tol=1e-8, sigma_damping=1.0,
-        p_damping=1.0, inner_tol=1e-8, sigma_fn=None, callback=None, diis=8, mix=0.5, diis_from=1e-3):
-    """Full GF2; returns the final GF2State (energies[] holds (E, E1, E2) per iteration)."""
+        p_damping=1.0, inner_tol=1e-8, sigma_fn=None, callback=None, diis=8, mix=0.5, diis_from=1e-3,
+        grid=None):
+    """Full GF2; returns the final GF2State (energies[] holds (E, E1, E2) per iteration).
+    ``grid`` = (M, index) replaces the uniform time grid of n_tau points."""
     n = system.nbf
     F, mu, G, P = inner_loop(system, F_start, None, None, None, beta, n_iw, inner_tol,
                              p_damping=p_damping, diis=diis, mix=mix, diis_from=diis_from)
     state = GF2State(F=F, mu=mu, P=P, G_iw=G, sig1=np.zeros((n, n)), sig2=np.zeros((n, n)))
     state.energies.append(energy(system, state, beta))
     for _ in range(max_outer):
-        _, Sig_tau = self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn)
+        _, Sig_tau = self_energy_step(system, state, beta, n_tau, n_iw, sigma_fn, grid)
         if state.Sigma_tau is not None and sigma_damping < 1.0:
             Sig_tau = sigma_damping * Sig_tau + (1.0 - sigma_damping) * state.Sigma_tau
         state.Sigma_tau = Sig_tau
-        state.Sigma_iw = tau_to_iw(Sig_tau, beta, n_iw)
-        state.sig1, state.sig2 = sigma_expansion(Sig_tau, beta)
+        state.Sigma_iw, state.sig1, state.sig2 = sigma_to_iw(Sig_tau, beta, n_iw, grid)
         state.F, state.mu, state.G_iw, state.P = inner_loop(
             system, state.F, state.Sigma_iw, state.sig1, state.sig2, beta, n_iw, inner_tol,
             p_damping=p_damping, diis=diis, mix=mix, diis_from=diis_from)

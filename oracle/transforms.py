@@ -24,6 +24,11 @@ the samples: on [tau_a, tau_{a+1}] the cubic through nodes a-1..a+2 (nodes
 0..3 on the first interval, M-3..M on the last), integrated exactly.  The
 same interpolant gives the expansion coefficients Sig1 = -(X(0)+X(beta)) and
 Sig2 = X'(0+) + X'(beta-).
+
+On a non-equidistant grid (``grids.power_mesh``) both directions keep these
+definitions: iw -> tau is the same sum evaluated at the grid's points, and
+tau -> iw integrates the same local cubics, now through unequally spaced
+nodes (``grid_fourier_weights``, ``sigma_expansion_grid``).
 """
 
 import numpy as np
@@ -178,3 +183,71 @@ def sigma_expansion(X_tau, beta):
     d0 = (-11.0 * x[0] + 18.0 * x[1] - 9.0 * x[2] + 2.0 * x[3]) / (6.0 * h)
     dM = (11.0 * x[M] - 18.0 * x[M - 1] + 9.0 * x[M - 2] - 2.0 * x[M - 3]) / (6.0 * h)
     return sig1, d0 + dM
+
+
+def grid_fourier_weights(beta, M, index, n_iw):
+    """[n_iw, n_tau] complex weights, X(i w_n) = sum_k Wt[n, k] X(tau_k), on the
+    grid tau_k = index[k] beta / M: on [tau_a, tau_a+1] the cubic through the
+    nodes a-1..a+2 (0..3 on the first interval, K-3..K on the last, K = n_tau - 1),
+    integrated exactly against e^{i w tau}.  With index = 0..M this is
+    ``cubic_fourier_weights``."""
+    idx = np.asarray(index, dtype=np.int64)
+    K = len(idx) - 1
+    w = matsubara(beta, n_iw)
+    n_idx = np.arange(n_iw)
+    Wt = np.zeros((n_iw, K + 1), dtype=np.complex128)
+    moments = {}
+    for a in range(K):
+        first = 0 if a == 0 else (K - 3 if a == K - 1 else a - 1)
+        nodes = list(range(first, first + 4))
+        r = int(idx[a + 1] - idx[a])                 # interval length in steps of beta / M
+        h = r * beta / M
+        offs = [(idx[j] - idx[a]) / r for j in nodes]
+        if r not in moments:
+            moments[r] = _monomial_moments(w * h)    # [4, n_iw]
+        integ = _lagrange_monomials(offs) @ moments[r]
+        ph = _phase(n_idx, [idx[a]], M, 1.0)[0]     # e^{i w_n tau_a}
+        for j, node in enumerate(nodes):
+            Wt[:, node] += h * ph * integ[j]
+    return Wt
+
+
+def tau_to_iw_grid(X_tau, beta, M, index, n_iw, chunk=1024):
+    """[n_iw, N, N] complex X(i w_n) from the samples on a non-equidistant grid."""
+    n_tau, n, _ = X_tau.shape
+    Wt = grid_fourier_weights(beta, M, index, n_iw)
+    flat = X_tau.reshape(n_tau, n * n)
+    out = np.empty((n_iw, n * n), dtype=np.complex128)
+    for i0 in range(0, n_iw, chunk):
+        out[i0:i0 + chunk] = Wt[i0:i0 + chunk] @ flat
+    return out.reshape(n_iw, n, n)
+
+
+def _lagrange_derivative(nodes, at):
+    """d/dtau of the Lagrange basis polynomials of ``nodes`` at ``at``."""
+    out = []
+    for j, tj in enumerate(nodes):
+        acc = 0.0
+        for m, tm in enumerate(nodes):
+            if m == j:
+                continue
+            term = 1.0 / (tj - tm)
+            for l, tl in enumerate(nodes):
+                if l != j and l != m:
+                    term *= (at - tl) / (tj - tl)
+            acc += term
+        out.append(acc)
+    return np.array(out)
+
+
+def sigma_expansion_grid(X_tau, beta, M, index):
+    """(Sig1, Sig2) of the interpolant on a non-equidistant grid: -(X(0)+X(beta))
+    and the slopes of the first and last cubics at tau = 0 and tau = beta."""
+    t = np.asarray(index, dtype=np.float64) * (beta / M)
+    K = len(t) - 1
+    sig1 = -(X_tau[0] + X_tau[K])
+    w0 = _lagrange_derivative(t[:4], t[0])
+    wK = _lagrange_derivative(t[K - 3:], t[K])
+    d0 = sum(w0[j] * X_tau[j] for j in range(4))
+    dK = sum(wK[j] * X_tau[K - 3 + j] for j in range(4))
+    return sig1, d0 + dK

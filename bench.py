@@ -68,8 +68,10 @@ def parse():
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
     ap.add_argument("--workload", default="h32_631g",
-                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma"])
+                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma", "h32_mesh"])
     ap.add_argument("--n-bf", type=int, default=128, help="basis size of --workload sigma")
+    ap.add_argument("--mesh", type=int, nargs=2, default=(7, 32), metavar=("P", "U"),
+                    help="power mesh of --workload h32_mesh (P halvings, U steps per interval)")
     ap.add_argument("--max-outer", type=int, default=30, help="outer GF2 iterations of --workload converge")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
@@ -817,6 +819,126 @@ def first_step_gpu(g, h, s, r, N, n_tau, n_iw, beta, prec, mu_hf=None):
     return s.e_nuc + e1 + e2, P, mu_hf, G_tau
 
 
+def run_mesh(args, rank, world, dist):
+    """The benchmark's system and step (H32 2x4x4 lattice, 6-31G, N = 64,
+    beta = 100, n_iw = 8192) on the non-equidistant time grid the paper uses
+    (Computational details): the uniform power mesh with --mesh P U (P halvings,
+    U steps per interval: 2 (P+1) U + 1 points on a uniform grid of 2^(P+1) U
+    intervals).  value = 8 N^5 n_points / step time; the energy and density are
+    checked against the oracle's first step on the same mesh and on the 4097-point
+    uniform grid (stored fixtures written from oracle/ only)."""
+    import torch
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    s, r = build_inputs()
+    p_, u_ = args.mesh
+    M, idx = g.power_mesh(p_, u_)
+    N, n_iw, beta = s.nbf, WORKLOAD["n_iw"], WORKLOAD["beta"]
+    n_tau = len(idx)
+    prec = PRECS[args.prec]
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    S, hcore, F0 = f64(s.S), f64(s.h), f64(r.F)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ctx = g.Context(N, None, n_iw, beta, grid=(M, idx))
+    h = ctx.handle
+    g.gf2_set_integrals(h, f64(s.eri))
+    g.gf2_set_overlap(h, S)
+    G_iw0 = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    P0 = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+    mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+    mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G_iw0, P0)
+    moments = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+    G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+    G_iw = torch.empty_like(G_iw0)
+    P = torch.empty_like(P0)
+    F_new = torch.empty_like(F0)
+
+    def step(out, pc, sev=None):
+        g.gf2_tail_moments(h, S, F0, mu_hf, None, moments)
+        g.gf2_fft_iw_to_tau(h, G_iw0, moments, G_tau)
+        if sev:
+            sev[0].record(stream)
+        g.gf2_sigma_tau(h, G_tau, Sig_tau, pc)
+        if sev:
+            sev[1].record(stream)
+        g.gf2_fft_tau_to_iw(h, Sig_tau, Sig_iw, sig12)
+        mu, nev = g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, G_iw, P)
+        g.gf2_fock(h, hcore, P, F_new)
+        e1, e2 = g.gf2_energy(h, hcore, F0, P, S, G_iw, Sig_iw, sig12)
+        out.append((s.e_nuc + e1 + e2, mu, nev))
+
+    log = []
+    for _ in range(args.warmup):
+        step(log, prec)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    g.gf2_profile(h, False)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    t0, t1 = ev(), ev()
+    sev = [(ev(), ev()) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(log, prec, sev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, dist)
+    sigma_ms = statistics.mean(a.elapsed_time(b) for a, b in sev)
+    E_split, P_split = log[-1][0], P.clone()
+    g.gf2_profile(h, True)
+    for _ in range(args.steps):
+        step(log, prec)
+    torch.cuda.synchronize()
+    prof, launches = g.gf2_profile_report(h)
+    g.gf2_profile(h, False)
+    # the same step with the FP64 GPU Sigma (and the other split precision)
+    checks = {}
+    for name in ["fp64"] + [x for x in ("fp16x3", "bf16x6") if x != args.prec]:
+        step(log, PRECS[name])
+        checks[name] = (log[-1][0], P.clone())
+    checks[args.prec] = (E_split, P_split)
+    fixtures = {}
+    for key, path in (("same_mesh", f"h32_631g_first_step_pm{p_}x{u_}_w{n_iw}.json"),
+                      ("uniform_4097", f"h32_631g_first_step_t4097_w{n_iw}.json")):
+        fp = os.path.join(ROOT, "tests", "golden", path)
+        if os.path.exists(fp):
+            d = json.load(open(fp))
+            P_or = torch.as_tensor(np.array(d["P"]), device="cuda")
+            fixtures[key] = {"fixture": os.path.relpath(fp, ROOT), "E_oracle": d["E"],
+                             **{name: {"abs_dE": abs(E - d["E"]), "max_abs_dP": (Pn - P_or).abs().max().item()}
+                                for name, (E, Pn) in checks.items()}}
+    useful = 8.0 * N ** 5 * n_tau
+    _, _, bf16_sust, _ = measured_peaks()
+    pair_sym = bool(np.abs(s.eri - s.eri.transpose(2, 3, 0, 1)).max() <= 1e-12 * np.abs(s.eri).max())
+    exec_frac = (4.0 * (1056.0 / 2048.0 if pair_sym else 1.0) + 4.0) / 8.0
+    line = {"metric": "GF2 iteration on the non-equidistant time grid (H32 6-31G)",
+            "value": useful / (ms_step * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+            "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
+            "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, n_iw={n_iw}, "
+                                    f"power mesh p={p_} u={u_}: {n_tau} time points on a {M}-interval grid"),
+                       "step": "one GF2 outer iteration, all hot-path rows",
+                       "parallelism": f"replicas x{world}"},
+            "sigma": {"s_per_iter": sigma_ms * 1e-3, "tflops_useful": useful / (sigma_ms * 1e-3) / 1e12,
+                      "issued_frac_of_bf16_build": useful * exec_frac * ISSUED[args.prec] / (sigma_ms * 1e-3)
+                      / 1e12 / bf16_sust},
+            "oracle_check": fixtures,
+            "kernels": {k: {"launches": c, "ms_per_step": ms / args.steps} for k, (c, ms) in prof.items()},
+            "gpu_launches": launches, "clocks": clocks, "mu_evaluations_per_step": log[-1][2]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_h64(args, rank, world, dist):
     """H64 4x4x4 lattice at 2.0 bohr, 6-31G (N = 128), beta = 200, n_tau = 8193,
     n_iw = 16384: one GF2 step through every row with the 128-wide split Sigma
@@ -1035,6 +1157,8 @@ def main():
         run_h32_sto3g(args, rank, world, dist)
     elif args.workload == "converge":
         run_converge(args, rank, world, dist)
+    elif args.workload == "h32_mesh":
+        run_mesh(args, rank, world, dist)
     elif args.workload == "h64":
         run_h64(args, rank, world, dist)
     elif args.workload == "sigma":

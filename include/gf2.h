@@ -79,11 +79,29 @@ typedef enum {
 typedef struct gf2_ctx gf2_ctx;
 
 /* Create a context for N basis functions (1 <= N <= 128), n_tau time points
- * (M = n_tau - 1 a power of two, 8 <= M <= 16384), n_iw >= 1 Matsubara
- * frequencies and inverse temperature
- * beta > 0, bound to the CUDA stream `stream` (a cudaStream_t; NULL = legacy
- * default stream) on the current device.  *out receives the context. */
+ * of the uniform grid tau_k = k beta / M (M = n_tau - 1 a power of two,
+ * 8 <= M <= 8192), 1 <= n_iw <= 2^20 Matsubara frequencies and inverse
+ * temperature beta > 0, bound to the CUDA stream `stream` (a cudaStream_t;
+ * NULL = legacy default stream) on the current device.  *out receives the
+ * context; GF2_ERR_ARG for sizes out of range (nothing is touched then). */
 gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, double beta, void *stream);
+
+/* The same on a non-equidistant time grid (the paper builds Sigma(tau) on a
+ * non-equidistant grid of a few thousand points, Computational details): the
+ * n_tau points tau_k = tau_index[k] beta / M, a subset of the uniform grid of
+ * M intervals (M a power of two, 8 <= M <= 8192).  h_tau_index: host array
+ * of n_tau ints (8 <= n_tau <= M + 1), strictly increasing from 0 to M and
+ * symmetric, tau_index[k] + tau_index[n_tau-1-k] = M (so that G(-tau_k) =
+ * -G(tau_{n_tau-1-k}) stays on the grid); copied, not kept.  The uniform
+ * power mesh (p halvings, u steps per interval: M = 2^(p+1) u, 2 (p+1) u + 1
+ * points) is the intended use.  On such a context gf2_fft_iw_to_tau writes
+ * the n_tau grid points, gf2_fft_tau_to_iw integrates the local cubics
+ * through the unequally spaced nodes (see there), and every other call works
+ * on the n_tau points unchanged.  GF2_ERR_ARG for an invalid grid,
+ * GF2_ERR_UNSUPPORTED when the transform's shared memory (16 M + 40 n_tau
+ * bytes) exceeds 227 KB. */
+gf2_status gf2_create_grid(gf2_ctx **out, int n_bf, int M, int n_tau, const int *h_tau_index, int n_iw,
+                           double beta, void *stream);
 gf2_status gf2_destroy(gf2_ctx *ctx);
 gf2_status gf2_set_stream(gf2_ctx *ctx, void *stream);
 const char *gf2_status_string(gf2_status s);
@@ -141,18 +159,21 @@ gf2_status gf2_tail_moments(gf2_ctx *ctx, const double *d_S, const double *d_F, 
  * T = the moment series of d_moments [4][N][N] resummed about a real pole
  * a = 1 hartree, T(z) = sum_r c_r (z - a)^-r, whose tau image is closed form.
  * Evaluated by one M-point FFT per matrix element (n_iw may exceed M; the
- * frequencies are folded modulo M).  d_X_iw [n_iw][N][N] c128 in,
- * d_X_tau [n_tau][N][N] out. */
+ * frequencies are folded modulo M) and written at the context's n_tau grid
+ * points.  d_X_iw [n_iw][N][N] c128 in, d_X_tau [n_tau][N][N] out. */
 gf2_status gf2_fft_iw_to_tau(gf2_ctx *ctx, const double *d_X_iw, const double *d_moments,
                              double *d_X_tau);
 
 /* Imaginary time -> Matsubara (Sigma(tau) -> Sigma(w) of step 3):
  *   X(i w_n) = int_0^beta e^{i w_n tau} X~(tau) dtau,
  * X~ = the piecewise-cubic interpolant of the samples (on [tau_a, tau_a+1]
- * the cubic through nodes a-1..a+2; nodes 0..3 and M-3..M at the ends),
- * integrated exactly: an M-point FFT times an attenuation factor plus
- * end-point corrections.  d_X_tau [n_tau][N][N] in, d_X_iw [n_iw][N][N] c128
- * out.  If d_sig12 is not NULL it receives [2][N][N] = (Sig1, Sig2), the
+ * the cubic through nodes a-1..a+2; nodes 0..3 and K-3..K at the ends,
+ * K = n_tau - 1), integrated exactly.  Uniform grid: an M-point FFT times an
+ * attenuation factor plus end-point corrections.  Non-equidistant grid
+ * (gf2_create_grid): each grid interval's cubic re-expanded on the uniform
+ * steps inside it, then two M-point FFTs of those coefficients (four real
+ * sequences) weighted by the exact monomial integrals of one step.
+ * d_X_tau [n_tau][N][N] in, d_X_iw [n_iw][N][N] c128 out.  If d_sig12 is not NULL it receives [2][N][N] = (Sig1, Sig2), the
  * 1/z and 1/z^2 coefficients of the result: Sig1 = -(X(0) + X(beta)),
  * Sig2 = X~'(0+) + X~'(beta-). */
 gf2_status gf2_fft_tau_to_iw(gf2_ctx *ctx, const double *d_X_tau, double *d_X_iw, double *d_sig12);

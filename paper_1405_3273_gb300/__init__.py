@@ -34,6 +34,7 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 _SIGS = {
     "gf2_create": [ctypes.POINTER(_P), _I, _I, _I, _D, _P],
+    "gf2_create_grid": [ctypes.POINTER(_P), _I, _I, _I, ctypes.POINTER(_I), _I, _D, _P],
     "gf2_destroy": [_P],
     "gf2_set_stream": [_P, _P],
     "gf2_status_string": [_I],
@@ -126,6 +127,34 @@ def gf2_create(n_bf, n_tau, n_iw, beta):
     if st != GF2_OK:
         raise GF2Error(st, "gf2_create rejected the sizes or could not allocate")
     return h
+
+
+def gf2_create_grid(n_bf, M, tau_index, n_iw, beta):
+    """Context on the non-equidistant grid tau_k = tau_index[k] beta / M (host ints)."""
+    idx = [int(i) for i in tau_index]
+    arr = (ctypes.c_int * len(idx))(*idx)
+    h = ctypes.c_void_p()
+    st = lib().gf2_create_grid(ctypes.byref(h), int(n_bf), int(M), len(idx), arr, int(n_iw), float(beta), _stream())
+    if st != GF2_OK:
+        raise GF2Error(st, "gf2_create_grid rejected the grid or the sizes, or could not allocate")
+    return h
+
+
+def power_mesh(p, u):
+    """(M, tau_index) of the uniform power mesh: [0, beta/2^(p+1)] and each
+    [beta/2^(j+1), beta/2^j], j = 1..p, cut into u equal steps, the upper half of
+    [0, beta] the mirror image; indices into the uniform grid of M = 2^(p+1) u
+    intervals (2 (p+1) u + 1 points)."""
+    if p < 0 or u < 1:
+        raise ValueError("power mesh needs p >= 0 and u >= 1")
+    M = (1 << (p + 1)) * u
+    lower, pos = [0], 0
+    for level in range(p + 1):                 # step 1 on the two innermost intervals, then 2, 4, ...
+        step = 1 << max(0, level - 1)
+        for _ in range(u):
+            pos += step
+            lower.append(pos)
+    return M, lower + [M - i for i in reversed(lower[:-1])]
 
 
 def gf2_destroy(ctx):
@@ -330,9 +359,15 @@ class Batch:
 class Context:
     """Owning handle around a gf2_ctx (destroyed on close / garbage collection)."""
 
-    def __init__(self, n_bf, n_tau, n_iw, beta):
-        self.n_bf, self.n_tau, self.n_iw, self.beta = int(n_bf), int(n_tau), int(n_iw), float(beta)
-        self.handle = gf2_create(n_bf, n_tau, n_iw, beta)
+    def __init__(self, n_bf, n_tau, n_iw, beta, grid=None):
+        """grid = (M, tau_index): a non-equidistant time grid (n_tau is then len(tau_index))."""
+        self.n_bf, self.n_iw, self.beta = int(n_bf), int(n_iw), float(beta)
+        if grid is None:
+            self.n_tau = int(n_tau)
+            self.handle = gf2_create(n_bf, n_tau, n_iw, beta)
+        else:
+            self.n_tau = len(grid[1])
+            self.handle = gf2_create_grid(n_bf, grid[0], grid[1], n_iw, beta)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

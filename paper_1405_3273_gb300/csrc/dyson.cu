@@ -653,7 +653,7 @@ gf2_status launch_density(gf2_ctx *ctx, const double *G, const double *coef, dou
                                                                   reinterpret_cast<const double2 *>(G), ctx->d_red)));
   GF2_CK_LAUNCH(ctx, "density_partial_kernel");
   density_final_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(
-      N2, nchunks, ctx->beta, ctx->d_red, coef, resum, ctx->d_tau_pole + 4 * (size_t)ctx->M, P);
+      N2, nchunks, ctx->beta, ctx->d_red, coef, resum, ctx->d_tau_pole + 4 * (size_t)(ctx->n_tau - 1), P);
   GF2_CK_LAUNCH(ctx, "density_final_kernel");
   return GF2_OK;
 }
@@ -717,7 +717,7 @@ static void launch_mu_body(gf2_ctx *ctx, cudaStream_t cs, const double *S, const
   density_partial_kernel<<<dim3((N2 + 127) / 128, nchunks), 128, 0, cs>>>(
       N2, n_iw, chunk, reinterpret_cast<const double2 *>(G), ctx->d_red, ms);
   density_final_kernel<<<(N2 + 255) / 256, 256, 0, cs>>>(N2, nchunks, ctx->beta, ctx->d_red, coef,
-                                                          ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)ctx->M,
+                                                          ctx->d_pole_resum, ctx->d_tau_pole + 4 * (size_t)(ctx->n_tau - 1),
                                                           P, ms, ctx->d_pole_resum + 4);
   trace_kernel<<<1, 256, 0, cs>>>(N, P, S, cnt);
   mu_control_kernel<<<1, 32, 0, cs>>>(ms, cnt, fl, loop);

@@ -74,7 +74,7 @@ void free_all(gf2_ctx *c) {
   c->prof_pool.clear();
   void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_v_split16, c->d_wt_split16, c->d_twiddle, c->d_iw_pole,
                   c->d_tau_pole, c->d_pole_resum, c->d_t2w_w, c->d_t2w_corr, c->d_ws,
-                  c->d_err, c->d_small, c->d_red};
+                  c->d_err, c->d_small, c->d_red, c->d_tau_index, c->d_fine_a, c->d_grid_lag, c->d_grid_mu};
   gf2_tc_release(c);
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -152,13 +152,10 @@ extern "C" const char *gf2_last_error(const gf2_ctx *ctx) {
   return ctx ? ctx->last_error.c_str() : "no context";
 }
 
-extern "C" gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, double beta, void *stream) {
-  if (!out) return GF2_ERR_ARG;
-  *out = nullptr;
-  const int M = n_tau - 1;
-  if (n_bf < 1 || n_bf > GF2_MAX_N || !is_pow2(M) || M < 8 || M > 8192 || n_iw < 1 ||
-      n_iw > (1 << 20) || !(beta > 0.0) || !std::isfinite(beta))
-    return GF2_ERR_ARG;
+// a context on the uniform grid (tau_index == nullptr, n_tau = M + 1) or on the
+// grid of n_tau points tau_k = tau_index[k] beta / M (validated by the caller)
+static gf2_status create_impl(gf2_ctx **out, int n_bf, int M, int n_tau, const int *tau_index, int n_iw,
+                              double beta, void *stream) {
   gf2_ctx *c = new (std::nothrow) gf2_ctx();
   if (!c) return GF2_ERR_NOMEM;
   c->N = n_bf;
@@ -182,7 +179,11 @@ extern "C" gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, d
   ck(cudaMalloc(&c->d_red, sizeof(double) * c->red_elems), "cudaMalloc(red)");
   ck(cudaMalloc(&c->d_err, sizeof(int) * 16), "cudaMalloc(err)");
   ck(cudaMallocHost(&c->h_pinned, sizeof(double) * 8), "cudaMallocHost");
-  if (st == GF2_OK) st = gf2_tables_build(c);
+  if (tau_index && st == GF2_OK) {
+    ck(cudaMalloc(&c->d_tau_index, sizeof(int) * n_tau), "cudaMalloc(tau_index)");
+    ck(cudaMemcpy(c->d_tau_index, tau_index, sizeof(int) * n_tau, cudaMemcpyHostToDevice), "tau_index upload");
+  }
+  if (st == GF2_OK) st = gf2_tables_build(c, tau_index);
   if (st == GF2_OK) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) st = gf2_cuda_fail(c, e, "gf2_create sync");
@@ -194,6 +195,32 @@ extern "C" gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, d
   }
   *out = c;
   return GF2_OK;
+}
+
+extern "C" gf2_status gf2_create(gf2_ctx **out, int n_bf, int n_tau, int n_iw, double beta, void *stream) {
+  if (!out) return GF2_ERR_ARG;
+  *out = nullptr;
+  const int M = n_tau - 1;
+  if (n_bf < 1 || n_bf > GF2_MAX_N || !is_pow2(M) || M < 8 || M > 8192 || n_iw < 1 ||
+      n_iw > (1 << 20) || !(beta > 0.0) || !std::isfinite(beta))
+    return GF2_ERR_ARG;
+  return create_impl(out, n_bf, M, n_tau, nullptr, n_iw, beta, stream);
+}
+
+extern "C" gf2_status gf2_create_grid(gf2_ctx **out, int n_bf, int M, int n_tau, const int *tau_index, int n_iw,
+                                      double beta, void *stream) {
+  if (!out) return GF2_ERR_ARG;
+  *out = nullptr;
+  if (n_bf < 1 || n_bf > GF2_MAX_N || !is_pow2(M) || M < 8 || M > 8192 || n_tau < 8 || n_tau > M + 1 ||
+      !tau_index || n_iw < 1 || n_iw > (1 << 20) || !(beta > 0.0) || !std::isfinite(beta))
+    return GF2_ERR_ARG;
+  if (tau_index[0] != 0 || tau_index[n_tau - 1] != M) return GF2_ERR_ARG;
+  for (int k = 0; k < n_tau; ++k) {
+    if (k > 0 && tau_index[k] <= tau_index[k - 1]) return GF2_ERR_ARG;   // strictly increasing
+    if (tau_index[k] + tau_index[n_tau - 1 - k] != M) return GF2_ERR_ARG;  // symmetric about beta / 2
+  }
+  if (gf2_grid_smem_bytes(M, n_tau) > 227 * 1024) return GF2_ERR_UNSUPPORTED;
+  return create_impl(out, n_bf, M, n_tau, tau_index, n_iw, beta, stream);
 }
 
 extern "C" gf2_status gf2_destroy(gf2_ctx *ctx) {

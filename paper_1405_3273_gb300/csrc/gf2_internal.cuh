@@ -83,6 +83,15 @@ struct gf2_ctx {
   double2 *d_t2w_w = nullptr;     // [n_iw]: h W(theta_n), attenuation factor
   double2 *d_t2w_corr = nullptr;  // [n_iw][8]: end corrections, nodes 0..3, M-3..M
 
+  // non-equidistant time grid (gf2_create_grid): the n_tau points as indices
+  // into the uniform grid of M intervals (nullptr: the uniform grid itself,
+  // n_tau = M + 1); the tables of the local-cubic Fourier integral on it
+  int *d_tau_index = nullptr;
+  int *d_fine_a = nullptr;         // [M]: the grid interval holding uniform interval f
+  double *d_grid_lag = nullptr;    // [n_tau - 1][4 nodes][4 powers]: local cubics in x = (tau - tau_a) / h_a
+  double2 *d_grid_mu = nullptr;    // [n_iw][4]: (beta / M) mu_q(w_n beta / M)
+  double grid_dw[8] = {};          // Sig2 weights: slopes at tau = 0 (nodes 0..3) and at beta (n_tau-4..n_tau-1)
+
   // FP64 Sigma workspace (two ping-pong buffers of chunk * N^4 doubles)
   double *d_ws = nullptr;
   size_t ws_elems = 0;
@@ -176,7 +185,9 @@ gf2_status gf2_dgemm(gf2_ctx *ctx, const Dgemm &g);
 gf2_status gf2_inverse_spd(gf2_ctx *ctx, const double *d_A, double *d_Ainv);
 
 // ---- internal entry points between translation units ----
-gf2_status gf2_tables_build(gf2_ctx *ctx);
+gf2_status gf2_tables_build(gf2_ctx *ctx, const int *h_tau_index);
+// shared memory of the tau -> iw kernel of a non-equidistant grid
+size_t gf2_grid_smem_bytes(int M, int n_tau);
 gf2_status gf2_pole_coefficients(gf2_ctx *ctx, const double *d_moments, double *d_coef);
 gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out);
 gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out,

@@ -168,7 +168,7 @@ gf2_status gf2_orth_transform_g(gf2_ctx *ctx, const double *d_G, int k0, int cou
   if (!ctx->d_orth_ws) GF2_CK(ctx, cudaMalloc(&ctx->d_orth_ws, 3 * grid * sizeof(double)));
   double *Go = ctx->d_orth_ws, *tmp = ctx->d_orth_ws + grid;
   const double *Sh = ctx->d_Shalf;
-  const int m0 = ctx->M - (k0 + count - 1);
+  const int m0 = (ctx->n_tau - 1) - (k0 + count - 1);  // G(-tau) = -G(beta - tau): the mirrored points
   gf2_status st;
   if (m0 <= k0 + count && k0 <= m0 + count) {  // the two ranges touch: one pass over the union
     const int lo = std::min(k0, m0), hi = std::max(k0, m0) + count;

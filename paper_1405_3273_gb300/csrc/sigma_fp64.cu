@@ -12,7 +12,7 @@
 
 gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G, int k0, int count, double *d_out) {
   const long long N = ctx->N, N2 = N * N, N3 = N2 * N, N4 = N3 * N;
-  const int M = ctx->M;
+  const int M = ctx->n_tau - 1;  // last grid point (tau = beta); the grid is symmetric about beta/2
   if (!ctx->d_ws) {
     size_t budget = (size_t)2 << 30;  // bytes for the two ping-pong buffers
     long long chunk = std::max<long long>(1, (long long)(budget / (2 * N4 * sizeof(double))));

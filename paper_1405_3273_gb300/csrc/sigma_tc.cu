@@ -1066,7 +1066,7 @@ gf2_status run_chunks(gf2_ctx *ctx, TcState *s, const double *d_G, int k0, int c
   // every slot of the call split in one launch, the whole output cleared once
   const int n_chunks = (count + C * B - 1) / (C * B);
   GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<NP, F><<<dim3(n_chunks * C, 2), 256, 0, ctx->stream>>>(
-                                 N, B, ctx->M, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
+                                 N, B, ctx->n_tau - 1, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
   GF2_CK_LAUNCH(ctx, "split_g_kernel");
   GF2_CK(ctx, cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)count * N * N, ctx->stream));
   for (int c0 = 0, sl0 = 0; c0 < count; c0 += C * B, sl0 += C) {

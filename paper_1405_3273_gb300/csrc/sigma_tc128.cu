@@ -758,7 +758,7 @@ gf2_status run128(gf2_ctx *ctx, TcState128 *s, const double *d_G, int k0, int co
   if (count <= 0) return GF2_OK;
   const int n_chunks = (count + C - 1) / C;
   GF2_PROF(ctx, GF2_K_SPLIT, (split_g_kernel<P, F><<<dim3(n_chunks * C, 2), 256, 0, ctx->stream>>>(
-                                 N, 1, ctx->M, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
+                                 N, 1, ctx->n_tau - 1, k0, count, S, d_G, s->Gs, s->gexp, ctx->vmax16)));
   GF2_CK_LAUNCH(ctx, "split_g_kernel");
   GF2_CK(ctx, cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)count * N * N, ctx->stream));
   for (int c0 = 0, sl0 = 0; c0 < count; c0 += C, sl0 += C) {

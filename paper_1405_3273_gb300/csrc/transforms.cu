@@ -17,8 +17,23 @@
 //             0..3, M-3..M and the interior formula.
 // The tables (twiddles, tail images, W, end corrections) depend only on the
 // grid and are built once per context.
+//
+// Non-equidistant grid (points tau_k = idx_k beta / M, a subset of the uniform
+// grid of M intervals, symmetric about beta / 2):
+// iw -> tau:  the same FFT over the M-interval grid, written at the points only.
+// tau -> iw:  the local cubics now pass through unequally spaced nodes.  On
+//             uniform interval f inside grid interval a (d = f - idx_a steps
+//             in, r = idx_a+1 - idx_a steps long) the cubic of a, in the local
+//             variable y = (tau - f h) / h, h = beta / M, has coefficients
+//             m'_fq = sum_{p >= q} m_ap binom(p, q) d^(p-q) / r^p (m_ap: its
+//             coefficients in x = (tau - tau_a) / h_a), so
+//             X(i w_n) = h sum_q mu_q(w_n h) D_q(n),
+//             D_q(n) = sum_f m'_fq e^{i w_n f h} = FFT_M(m'_fq e^{i pi f / M})(n mod M),
+//             two real sequences per complex FFT (q = 0,1 then q = 2,3),
+//             separated by D(n) = [Z(n) +- conj Z(M-1-n)] / (2 or 2i).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "gf2_internal.cuh"
 
@@ -79,7 +94,7 @@ __device__ double2 interval_weight(const double (*lag)[4], int o_idx, const doub
 
 __global__ void tables_kernel(int M, int n_tau, int n_iw, double beta, double a, double2 *twiddle,
                               double2 *iw_pole, double *tau_pole, double2 *t2w_w,
-                              double2 *t2w_corr, double2 *halfphase) {
+                              double2 *t2w_corr, double2 *halfphase, const int *tau_index) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const double h = beta / M;
   if (tid < M / 2) {
@@ -93,7 +108,7 @@ __global__ void tables_kernel(int M, int n_tau, int n_iw, double beta, double a,
     halfphase[tid] = make_double2(c, -s);  // e^{-i pi k / M}
   }
   if (tid < n_tau) {
-    const double t = tid * h;
+    const double t = (tau_index ? tau_index[tid] : tid) * h;
     const double E = exp(-a * t), q = exp(-a * beta);
     const double u = 1.0 / (1.0 + q), v = u * (q / (1.0 + q));
     const double u1 = beta * v, u2 = beta * beta * v * (1.0 - 2.0 * u);
@@ -187,7 +202,7 @@ __global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, doub
                                  const double2 *__restrict__ X_iw, const double *__restrict__ coef,
                                  const double2 *__restrict__ iw_pole, const double *__restrict__ tau_pole,
                                  const double2 *__restrict__ tw, const double2 *__restrict__ halfphase,
-                                 double *__restrict__ X_tau) {
+                                 int n_tau, const int *__restrict__ tau_index, double *__restrict__ X_tau) {
   extern __shared__ double2 sm[];
   double2 *x = sm;                              // [E][M]
   double *c = reinterpret_cast<double *>(x + (size_t)E * M);  // [E][4]
@@ -213,14 +228,15 @@ __global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, doub
   __syncthreads();
   fft_dif_smem(x, E, M, tw, -1);
   const double s2b = 2.0 / beta;
-  for (int idx = threadIdx.x; idx < E * (M + 1); idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < E * n_tau; idx += blockDim.x) {
     const int k = idx / E, e = idx - k * E;
+    const int j = tau_index ? tau_index[k] : k;  // the point on the uniform grid
     const double *ce = c + 4 * e;
     double val;
-    if (k < M) {
-      const int br = (int)(__brev((unsigned)k) >> (32 - log2M));
+    if (j < M) {
+      const int br = (int)(__brev((unsigned)j) >> (32 - log2M));
       const double2 z = x[(size_t)e * M + br];
-      const double2 ph = halfphase[k];
+      const double2 ph = halfphase[j];
       val = s2b * (z.x * ph.x - z.y * ph.y);
     } else {
       val = -s2b * x[(size_t)e * M].x;
@@ -280,6 +296,101 @@ __global__ void sigma_ends_kernel(int N2, int M, double h, const double *X, doub
   sig12[(size_t)N2 + e] = d0 + dM;
 }
 
+// [n_iw][4]: h mu_q(w_n h), h = beta / M (the uniform step)
+__global__ void grid_mu_kernel(int n_iw, int M, double beta, double2 *out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_iw) return;
+  const double h = beta / M;
+  double2 mu[4];
+  monomial_moments((2.0 * n + 1.0) * M_PI / (double)M, mu);  // w_n h
+  for (int q = 0; q < 4; ++q) out[4 * (size_t)n + q] = cscale(mu[q], h);
+}
+
+// tau -> iw on a non-equidistant grid of K + 1 points, one matrix element per
+// CTA: the node values, the cubic of every grid interval, then two passes of
+// (expand onto the uniform intervals, FFT, accumulate X(i w_n)).
+__global__ void tau_to_iw_grid_kernel(int N2, int M, int log2M, int K, int n_iw,
+                                      const double *__restrict__ X_tau, const double2 *__restrict__ tw,
+                                      const double2 *__restrict__ halfphase, const double *__restrict__ lag,
+                                      const int *__restrict__ tau_index, const int *__restrict__ fine_a,
+                                      const double2 *__restrict__ gmu, double2 *__restrict__ X_iw) {
+  extern __shared__ double2 sm[];
+  double2 *x = sm;                                           // [M]
+  double *xs = reinterpret_cast<double *>(x + M);            // [K + 1] node values
+  double *mc = xs + (K + 1);                                 // [K][4] cubic of each interval
+  const int e = blockIdx.x;
+  for (int k = threadIdx.x; k <= K; k += blockDim.x) xs[k] = X_tau[(size_t)k * N2 + e];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * K; i += blockDim.x) {
+    const int a = i >> 2, p = i & 3;
+    const int first = a == 0 ? 0 : (a == K - 1 ? K - 3 : a - 1);
+    const double *c = lag + 16 * (size_t)a;  // [4 nodes][4 powers]
+    mc[i] = c[p] * xs[first] + c[4 + p] * xs[first + 1] + c[8 + p] * xs[first + 2] + c[12 + p] * xs[first + 3];
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int f = threadIdx.x; f < M; f += blockDim.x) {
+      const int a = fine_a[f];
+      const int i0 = tau_index[a];
+      const double ir = 1.0 / (double)(tau_index[a + 1] - i0), d = (double)(f - i0);
+      // the cubic of interval a in y = (tau - f h) / h: powers of (d + y) / r
+      const double m1 = mc[4 * a + 1] * ir, m2 = mc[4 * a + 2] * ir * ir, m3 = mc[4 * a + 3] * ir * ir * ir;
+      double lo, hi;
+      if (pass == 0) {
+        lo = mc[4 * a] + d * (m1 + d * (m2 + d * m3));
+        hi = m1 + d * (2.0 * m2 + 3.0 * d * m3);
+      } else {
+        lo = m2 + 3.0 * d * m3;
+        hi = m3;
+      }
+      const double2 ph = halfphase[f];  // e^{-i pi f / M}; the twist is its conjugate
+      x[f] = make_double2(lo * ph.x + hi * ph.y, hi * ph.x - lo * ph.y);
+    }
+    __syncthreads();
+    fft_dif_smem(x, 1, M, tw, +1);
+    for (int n = threadIdx.x; n < n_iw; n += blockDim.x) {
+      const int j = n & (M - 1), jm = M - 1 - j;
+      const double2 z = x[__brev((unsigned)j) >> (32 - log2M)];
+      const double2 zm = x[__brev((unsigned)jm) >> (32 - log2M)];
+      const double2 A = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));   // (Z + conj Zm) / 2
+      const double2 B = make_double2(0.5 * (z.y + zm.y), -0.5 * (z.x - zm.x));  // (Z - conj Zm) / 2i
+      const double2 *mu = gmu + 4 * (size_t)n + 2 * pass;
+      const double2 val = cadd(cmul(mu[0], A), cmul(mu[1], B));
+      double2 *out = X_iw + (size_t)n * N2 + e;
+      *out = pass == 0 ? val : cadd(*out, val);
+    }
+    __syncthreads();
+  }
+}
+
+// Sig1 = -(X_0 + X_K), Sig2 = the slopes of the end cubics (weights w[0..7])
+struct SlopeWeights {
+  double w[8];
+};
+__global__ void sigma_ends_grid_kernel(int N2, int K, SlopeWeights sw, const double *X, double *sig12) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N2) return;
+  double d = 0.0;
+  for (int j = 0; j < 4; ++j)
+    d += sw.w[j] * X[(size_t)j * N2 + e] + sw.w[4 + j] * X[(size_t)(K - 3 + j) * N2 + e];
+  sig12[e] = -(X[e] + X[(size_t)K * N2 + e]);
+  sig12[(size_t)N2 + e] = d;
+}
+
+// monomial coefficients c[j][p] (powers of x) of the Lagrange basis of the nodes s[0..3]
+void lagrange_monomials(const double s[4], double c[4][4]) {
+  for (int j = 0; j < 4; ++j) {
+    double poly[4] = {1.0, 0.0, 0.0, 0.0}, denom = 1.0;
+    for (int m = 0; m < 4; ++m) {
+      if (m == j) continue;
+      for (int p = 3; p >= 1; --p) poly[p] = poly[p - 1] - s[m] * poly[p];  // times (x - s_m)
+      poly[0] = -s[m] * poly[0];
+      denom *= s[j] - s[m];
+    }
+    for (int p = 0; p < 4; ++p) c[j][p] = poly[p] / denom;
+  }
+}
+
 int pick_elems_per_cta(int N2, int M) {
   const size_t budget = 130 * 1024;
   for (int E = 4; E >= 1; E >>= 1)
@@ -289,7 +400,43 @@ int pick_elems_per_cta(int N2, int M) {
 
 }  // namespace
 
-gf2_status gf2_tables_build(gf2_ctx *ctx) {
+size_t gf2_grid_smem_bytes(int M, int n_tau) {
+  return sizeof(double2) * (size_t)M + sizeof(double) * (size_t)n_tau + sizeof(double) * 4 * (size_t)(n_tau - 1);
+}
+
+// the host-side tables of a non-equidistant grid: each interval's local cubic
+// (nodes a-1..a+2, 0..3 first, K-3..K last, offsets in units of its length),
+// the interval of every uniform step, and the end slopes of Sig2
+static gf2_status grid_tables(gf2_ctx *ctx, const int *idx) {
+  const int M = ctx->M, K = ctx->n_tau - 1;
+  std::vector<double> lag(16 * (size_t)K);
+  std::vector<int> fine_a(M);
+  for (int a = 0; a < K; ++a) {
+    const int first = a == 0 ? 0 : (a == K - 1 ? K - 3 : a - 1);
+    const double r = (double)(idx[a + 1] - idx[a]);
+    double s[4], c[4][4];
+    for (int j = 0; j < 4; ++j) s[j] = (double)(idx[first + j] - idx[a]) / r;
+    lagrange_monomials(s, c);
+    for (int j = 0; j < 4; ++j)
+      for (int p = 0; p < 4; ++p) lag[16 * (size_t)a + 4 * j + p] = c[j][p];
+    for (int f = idx[a]; f < idx[a + 1]; ++f) fine_a[f] = a;
+    const double h = r * ctx->beta / M;
+    if (a == 0)
+      for (int j = 0; j < 4; ++j) ctx->grid_dw[j] = c[j][1] / h;  // d/dtau at x = 0
+    if (a == K - 1)
+      for (int j = 0; j < 4; ++j) ctx->grid_dw[4 + j] = (c[j][1] + 2.0 * c[j][2] + 3.0 * c[j][3]) / h;  // at x = 1
+  }
+  GF2_CK(ctx, cudaMalloc(&ctx->d_grid_lag, sizeof(double) * lag.size()));
+  GF2_CK(ctx, cudaMalloc(&ctx->d_fine_a, sizeof(int) * M));
+  GF2_CK(ctx, cudaMalloc(&ctx->d_grid_mu, sizeof(double2) * 4 * (size_t)ctx->n_iw));
+  GF2_CK(ctx, cudaMemcpy(ctx->d_grid_lag, lag.data(), sizeof(double) * lag.size(), cudaMemcpyHostToDevice));
+  GF2_CK(ctx, cudaMemcpy(ctx->d_fine_a, fine_a.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
+  grid_mu_kernel<<<(ctx->n_iw + 127) / 128, 128, 0, ctx->stream>>>(ctx->n_iw, M, ctx->beta, ctx->d_grid_mu);
+  GF2_CK_LAUNCH(ctx, "grid_mu_kernel");
+  return GF2_OK;
+}
+
+gf2_status gf2_tables_build(gf2_ctx *ctx, const int *h_tau_index) {
   const int M = ctx->M, n_tau = ctx->n_tau, n_iw = ctx->n_iw;
   GF2_CK(ctx, cudaMalloc(&ctx->d_twiddle, sizeof(double2) * (M / 2 + M)));
   GF2_CK(ctx, cudaMalloc(&ctx->d_iw_pole, sizeof(double2) * 4 * (size_t)n_iw));
@@ -300,8 +447,12 @@ gf2_status gf2_tables_build(gf2_ctx *ctx) {
   const int total = std::max(std::max(M, n_tau), n_iw);
   tables_kernel<<<(total + 127) / 128, 128, 0, ctx->stream>>>(
       M, n_tau, n_iw, ctx->beta, GF2_TAIL_POLE, ctx->d_twiddle, ctx->d_iw_pole, ctx->d_tau_pole,
-      ctx->d_t2w_w, ctx->d_t2w_corr, ctx->d_twiddle + M / 2);
+      ctx->d_t2w_w, ctx->d_t2w_corr, ctx->d_twiddle + M / 2, ctx->d_tau_index);
   GF2_CK_LAUNCH(ctx, "tables_kernel");
+  if (h_tau_index) {
+    gf2_status st = grid_tables(ctx, h_tau_index);
+    if (st != GF2_OK) return st;
+  }
   pole_resum_kernel<<<1, 256, 0, ctx->stream>>>(n_iw, ctx->d_iw_pole, ctx->d_pole_resum);
   GF2_CK_LAUNCH(ctx, "pole_resum_kernel");
   // the lowest n_iw / 8 frequencies serve the coarse counts of the mu search
@@ -327,7 +478,8 @@ extern "C" gf2_status gf2_fft_iw_to_tau(gf2_ctx *ctx, const double *d_X_iw, cons
   GF2_PROF(ctx, GF2_K_IW2TAU,
            (iw_to_tau_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
                N2, M, ctx->log2M, ctx->n_iw, E, ctx->beta, reinterpret_cast<const double2 *>(d_X_iw), coef,
-               ctx->d_iw_pole, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, d_X_tau)));
+               ctx->d_iw_pole, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->n_tau,
+               ctx->d_tau_index, d_X_tau)));
   GF2_CK_LAUNCH(ctx, "iw_to_tau_kernel");
   return GF2_OK;
 }
@@ -336,6 +488,23 @@ extern "C" gf2_status gf2_fft_tau_to_iw(gf2_ctx *ctx, const double *d_X_tau, dou
   if (!ctx) return GF2_ERR_ARG;
   if (!d_X_tau || !d_X_iw) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_fft_tau_to_iw: NULL pointer");
   const int N2 = ctx->N * ctx->N, M = ctx->M;
+  if (ctx->d_tau_index) {  // non-equidistant grid
+    const int K = ctx->n_tau - 1;
+    const size_t smem = gf2_grid_smem_bytes(M, ctx->n_tau);
+    GF2_CK(ctx, cudaFuncSetAttribute(tau_to_iw_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GF2_PROF(ctx, GF2_K_TAU2IW,
+             (tau_to_iw_grid_kernel<<<N2, 512, smem, ctx->stream>>>(
+                 N2, M, ctx->log2M, K, ctx->n_iw, d_X_tau, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->d_grid_lag,
+                 ctx->d_tau_index, ctx->d_fine_a, ctx->d_grid_mu, reinterpret_cast<double2 *>(d_X_iw))));
+    GF2_CK_LAUNCH(ctx, "tau_to_iw_grid_kernel");
+    if (d_sig12) {
+      SlopeWeights sw;
+      for (int j = 0; j < 8; ++j) sw.w[j] = ctx->grid_dw[j];
+      sigma_ends_grid_kernel<<<(N2 + 255) / 256, 256, 0, ctx->stream>>>(N2, K, sw, d_X_tau, d_sig12);
+      GF2_CK_LAUNCH(ctx, "sigma_ends_grid_kernel");
+    }
+    return GF2_OK;
+  }
   const int E = pick_elems_per_cta(N2, M);
   const size_t smem = (size_t)E * M * sizeof(double2) + sizeof(double) * 8 * E;
   GF2_CK(ctx, cudaFuncSetAttribute(tau_to_iw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

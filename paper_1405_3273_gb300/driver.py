@@ -29,17 +29,19 @@ class DeviceSystem:
     n_tau: int
     n_iw: int
     mu0: float
+    grid: tuple = None   # (M, tau_index): a non-equidistant time grid replacing the n_tau uniform points
 
     @property
     def nbf(self):
         return self.S.shape[0]
 
 
-def to_device(system, F_start, mu0, device="cuda"):
+def to_device(system, F_start, mu0, device="cuda", grid=None):
     f = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+    n_tau = int(system.n_tau) if grid is None else len(grid[1])
     return DeviceSystem(S=f(system.S), h=f(system.h), v=f(system.eri), F0=f(F_start),
                         e_nuc=float(system.e_nuc), n_elec=int(system.n_elec), beta=float(system.beta),
-                        n_tau=int(system.n_tau), n_iw=int(system.n_iw), mu0=float(mu0))
+                        n_tau=n_tau, n_iw=int(system.n_iw), mu0=float(mu0), grid=grid)
 
 
 @dataclass
@@ -64,7 +66,7 @@ class GF2Run:
 
 def start(sys, prec=GF2_PREC_FP64):
     n, nt, nw = sys.nbf, sys.n_tau, sys.n_iw
-    ctx = Context(n, nt, nw, sys.beta)
+    ctx = Context(n, nt, nw, sys.beta, grid=sys.grid)
     gf2_set_integrals(ctx.handle, sys.v)
     gf2_set_overlap(ctx.handle, sys.S)
     dev = sys.S.device

@@ -15,8 +15,13 @@ only (``oracle/``; no GPU code is imported):
   6. Galitskii-Migdal energy E = E_nuc + 1/2 Tr[P (h + F_HF)] + E2.
 
 Usage:  python tests/golden/make_h32_631g_first_step.py [--n-tau 4097 --n-iw 8192]
+                                                        [--mesh P U]
 The full grid takes about 20 minutes on 8 cores (Sigma at 4097 time points
-dominates).  Output: tests/golden/h32_631g_first_step_t{n_tau}_w{n_iw}.json.
+dominates).  Output: tests/golden/h32_631g_first_step_t{n_tau}_w{n_iw}.json,
+or with --mesh the same step on the uniform power mesh with P halvings and U
+steps per interval (``oracle.grids.power_mesh``; iw -> tau at the mesh
+points, the local-cubic integral through its unequal nodes):
+tests/golden/h32_631g_first_step_pm{P}x{U}_w{n_iw}.json.
 """
 
 import argparse
@@ -33,16 +38,19 @@ sys.path.insert(0, ROOT)
 
 import gf2_inputs as gi  # noqa: E402
 from oracle import dyson as od  # noqa: E402
+from oracle import grids as og  # noqa: E402
 from oracle import energy as oe  # noqa: E402
 from oracle import sigma as osg  # noqa: E402
 from oracle import transforms as ot  # noqa: E402
 
 
-def fixture_path(n_tau, n_iw):
+def fixture_path(n_tau, n_iw, mesh=None):
+    if mesh is not None:
+        return os.path.join(HERE, f"h32_631g_first_step_pm{mesh[0]}x{mesh[1]}_w{n_iw}.json")
     return os.path.join(HERE, f"h32_631g_first_step_t{n_tau}_w{n_iw}.json")
 
 
-def first_step(n_tau, n_iw, beta=100.0, spacing=2.0):
+def first_step(n_tau, n_iw, beta=100.0, spacing=2.0, mesh=None):
     t0 = time.time()
     s = gi.build_system("h32_lattice_631g", spacing=spacing)
     r = gi.rhf(s)
@@ -50,10 +58,19 @@ def first_step(n_tau, n_iw, beta=100.0, spacing=2.0):
     mu0, G0, P0, nev0 = od.mu_search(s.S, F, None, None, None, s.n_elec, beta, n_iw)
     e_hf = s.e_nuc + oe.e_one_body(P0, s.h, F)
     mom = ot.tail_moments(s.S, F, mu0)
-    G_tau = ot.iw_to_tau(G0, mom, beta, n_tau)
+    if mesh is None:
+        G_tau = ot.iw_to_tau(G0, mom, beta, n_tau)
+    else:
+        M, index = og.power_mesh(*mesh)
+        n_tau = len(index)
+        G_tau = ot.iw_to_tau(G0, mom, beta, M + 1, taus=index)
     Sig_tau = osg.sigma_tau(G_tau, s.eri)
-    Sig_iw = ot.tau_to_iw(Sig_tau, beta, n_iw)
-    sig1, sig2 = ot.sigma_expansion(Sig_tau, beta)
+    if mesh is None:
+        Sig_iw = ot.tau_to_iw(Sig_tau, beta, n_iw)
+        sig1, sig2 = ot.sigma_expansion(Sig_tau, beta)
+    else:
+        Sig_iw = ot.tau_to_iw_grid(Sig_tau, beta, M, index, n_iw)
+        sig1, sig2 = ot.sigma_expansion_grid(Sig_tau, beta, M, index)
     mu, G, P, nev = od.mu_search(s.S, F, Sig_iw, sig1, sig2, s.n_elec, beta, n_iw)
     e1 = oe.e_one_body(P, s.h, F)
     e2 = oe.e_two_body(G, Sig_iw, sig1, s.S, beta)
@@ -63,6 +80,7 @@ def first_step(n_tau, n_iw, beta=100.0, spacing=2.0):
                  "H32 2x4x4 lattice at 2.0 bohr, 6-31G (N=64), beta=100; F held at F_HF"),
         "written_by": "tests/golden/make_h32_631g_first_step.py (calls oracle/ and gf2_inputs only)",
         "n_bf": int(s.nbf), "n_elec": int(s.n_elec), "beta": beta, "n_tau": n_tau, "n_iw": n_iw,
+        "mesh": None if mesh is None else {"p": mesh[0], "u": mesh[1], "M": int(M)},
         "spacing_bohr": spacing,
         "mu_hf": mu0, "E_hf": e_hf, "P_hf_trace_PS": float(np.trace(P0 @ s.S)),
         "mu": mu, "E": s.e_nuc + e1 + e2, "E_one_body": e1, "E_two_body": e2, "E_nuc": s.e_nuc,
@@ -80,9 +98,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n-tau", type=int, default=4097)
     ap.add_argument("--n-iw", type=int, default=8192)
+    ap.add_argument("--mesh", type=int, nargs=2, default=None, metavar=("P", "U"))
     a = ap.parse_args()
-    d = first_step(a.n_tau, a.n_iw)
-    with open(fixture_path(a.n_tau, a.n_iw), "w") as f:
+    mesh = tuple(a.mesh) if a.mesh else None
+    d = first_step(a.n_tau, a.n_iw, mesh=mesh)
+    with open(fixture_path(a.n_tau, a.n_iw, mesh), "w") as f:
         json.dump(d, f, indent=0)
     print(json.dumps({k: v for k, v in d.items() if k not in ("P", "sigma_tau_samples")}))
 

@@ -84,3 +84,27 @@ def test_batch_create_rejects_bad_sizes_before_touching_the_device(library):
     assert h.value is None
     assert f(ctypes.byref(h), 1, ints(10), ints(100), None) == 1             # M = 99 not a power of two
     assert h.value is None
+
+
+def test_create_grid_rejects_bad_grids_before_touching_the_device(library):
+    f = library.gf2_create_grid
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+
+    def call(M, idx, n_bf=4, n_iw=64, beta=10.0):
+        arr = (ctypes.c_int * len(idx))(*idx) if idx is not None else None
+        return f(ctypes.byref(h), n_bf, M, len(idx) if idx is not None else 9, arr, n_iw, beta, None)
+
+    good = [0, 1, 2, 4, 8, 12, 14, 15, 16]
+    assert call(16, good[:-1] + [15]) == 1                  # does not end at M
+    assert call(16, [1] + good[1:]) == 1                    # does not start at 0
+    assert call(16, [0, 1, 2, 4, 8, 13, 14, 15, 16]) == 1   # not symmetric about beta / 2
+    assert call(16, [0, 1, 2, 8, 4, 12, 14, 15, 16]) == 1   # not increasing
+    assert call(12, [0, 1, 2, 3, 6, 9, 10, 11, 12]) == 1    # M not a power of two
+    assert call(16, [0, 2, 8, 14, 16]) == 1                 # fewer than 8 points
+    assert call(16, None) == 1                              # NULL index
+    assert call(16, good, n_bf=0) == 1
+    assert call(16, good, beta=0.0) == 1
+    assert h.value is None

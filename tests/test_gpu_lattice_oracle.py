@@ -15,7 +15,10 @@ there each time point carries sixteen times the quadrature weight of
 Sigma(tau) -> Sigma(i w), and the split rounding errors of the points, which
 are independent, add up to sqrt(16) = 4 times the density error of the full
 grid, so the density bound there is 4e-6 (the measured FP16x3 error is 6e-7
-on the full grid and 3.4e-6 on the reduced one).
+on the full grid and 3.4e-6 on the reduced one).  The same scaling with the
+point count covers the ``..._pm{p}x{u}_...`` fixtures: the step on the uniform
+power mesh with p halvings and u steps per interval (the non-equidistant
+grid), which the GPU runs on a context made by gf2_create_grid.
 """
 
 import glob
@@ -31,7 +34,8 @@ import gf2_inputs as gi
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-FIXTURES = sorted(glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_t*_w*.json")))
+FIXTURES = sorted(glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_t*_w*.json")) +
+                  glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_pm*_w*.json")))
 BOUNDS = {0: (1e-8, 1e-8), 2: (1e-6, 1e-6), 3: (1e-6, 1e-6), 4: (1e-6, 1e-6)}
 
 
@@ -46,12 +50,12 @@ def lattice():
     return g, s, gi.rhf(s)
 
 
-def first_step(g, s, r, n_tau, n_iw, beta, precs):
+def first_step(g, s, r, n_tau, n_iw, beta, precs, grid=None):
     f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     N = s.nbf
     S, hc, F0 = f64(s.S), f64(s.h), f64(r.F)
     out = {}
-    with g.Context(N, n_tau, n_iw, beta) as ctx:
+    with g.Context(N, n_tau, n_iw, beta, grid=grid) as ctx:
         h = ctx.handle
         g.gf2_set_integrals(h, f64(s.eri))
         g.gf2_set_overlap(h, S)
@@ -86,7 +90,11 @@ def test_first_step_matches_oracle(lattice, path):
     assert ref["n_bf"] == s.nbf == 64
     n_tau, n_iw, beta = ref["n_tau"], ref["n_iw"], ref["beta"]
     P_ref = np.array(ref["P"])
-    got = first_step(g, s, r, n_tau, n_iw, beta, sorted(BOUNDS))
+    grid = None
+    if ref.get("mesh"):
+        grid = g.power_mesh(ref["mesh"]["p"], ref["mesh"]["u"])
+        assert grid[0] == ref["mesh"]["M"] and len(grid[1]) == n_tau
+    got = first_step(g, s, r, n_tau, n_iw, beta, sorted(BOUNDS), grid)
     e_hf, P_hf = got["hf"]
     assert abs(e_hf - ref["E_hf"]) < 1e-9
     assert abs(np.trace(P_hf @ s.S) - s.n_elec) <= 1e-10

@@ -74,7 +74,7 @@ void free_all(gf2_ctx *c) {
   c->prof_pool.clear();
   void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_v_split16, c->d_wt_split16, c->d_twiddle, c->d_iw_pole,
                   c->d_tau_pole, c->d_pole_resum, c->d_t2w_w, c->d_t2w_corr, c->d_ws,
-                  c->d_err, c->d_small, c->d_red, c->d_tau_index, c->d_fine_a, c->d_grid_lag, c->d_grid_mu};
+                  c->d_err, c->d_small, c->d_red, c->d_tau_index, c->d_fine_a, c->d_grid_lag, c->d_grid_mu, c->d_iw_pole_fold};
   gf2_tc_release(c);
   for (void *p : ptrs)
     if (p) cudaFree(p);

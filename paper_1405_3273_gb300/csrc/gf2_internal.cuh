@@ -77,6 +77,7 @@ struct gf2_ctx {
   // grid tables (built at create)
   double2 *d_twiddle = nullptr;   // e^{-2 pi i k / M}, k < M/2
   double2 *d_iw_pole = nullptr;   // [n_iw][4]: (i w_n - a)^-(r+1)
+  double2 *d_iw_pole_fold = nullptr;  // [M][4]: sum over n = j mod M, n < n_iw, of (i w_n - a)^-(r+1)
   double *d_tau_pole = nullptr;   // [n_tau][4]: tau image of (z - a)^-(r+1)
   double *d_pole_resum = nullptr; // [8]: sum_{n<n_iw}, then sum_{n<n_coarse}, of Re (i w_n - a)^-(r+1)
   int n_coarse = 0;               // frequencies of a coarse particle count (0: none)

@@ -7,6 +7,7 @@
 //
 // iw -> tau:  X(tau_k) = (2/beta) Re[e^{-i pi k/M} Z_k] + T(tau_k),
 //             Z = FFT_M(Y),  Y_j = sum_{n = j mod M, n < n_iw} (X - T)(i w_n)
+//             (the tail's folded sums per j are a table: Y_j = sum X - sum_r c_r Q_jr)
 //             (w_n tau_k = pi (2n+1) k / M, so frequencies fold modulo M;
 //             tau_M = beta uses e^{-i pi (2n+1)} = -1).
 // tau -> iw:  the exact Fourier integral of the piecewise-cubic interpolant:
@@ -198,9 +199,19 @@ __device__ void fft_dif_smem(double2 *x, int E, int M, const double2 *tw, int si
   }
 }
 
+// the pole terms folded like the frequencies: Q[j][r] = sum_{n = j mod M, n < n_iw} (i w_n - a)^-(r+1)
+__global__ void pole_fold_kernel(int M, int n_iw, const double2 *__restrict__ iw_pole, double2 *__restrict__ fold) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  double2 q[4] = {};
+  for (int n = j; n < n_iw; n += M)
+    for (int r = 0; r < 4; ++r) q[r] = cadd(q[r], iw_pole[4 * (size_t)n + r]);
+  for (int r = 0; r < 4; ++r) fold[4 * (size_t)j + r] = q[r];
+}
+
 __global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, double beta,
                                  const double2 *__restrict__ X_iw, const double *__restrict__ coef,
-                                 const double2 *__restrict__ iw_pole, const double *__restrict__ tau_pole,
+                                 const double2 *__restrict__ pole_fold, const double *__restrict__ tau_pole,
                                  const double2 *__restrict__ tw, const double2 *__restrict__ halfphase,
                                  int n_tau, const int *__restrict__ tau_index, double *__restrict__ X_tau) {
   extern __shared__ double2 sm[];
@@ -216,12 +227,13 @@ __global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, doub
     const int j = idx / E, e = idx - j * E;
     const double *ce = c + 4 * e;
     double2 acc = make_double2(0.0, 0.0);
-    for (int n = j; n < n_iw; n += M) {
-      const double2 v = X_iw[(size_t)n * N2 + e0 + e];
-      const double2 *p = iw_pole + 4 * (size_t)n;
-      double2 t = cadd(cadd(cscale(p[0], ce[0]), cscale(p[1], ce[1])),
-                       cadd(cscale(p[2], ce[2]), cscale(p[3], ce[3])));
-      acc = cadd(acc, csub(v, t));
+    for (int n = j; n < n_iw; n += M) acc = cadd(acc, X_iw[(size_t)n * N2 + e0 + e]);
+    // minus the tail, folded the same way: sum_r c_r Q[j][r]
+    const double2 *q = pole_fold + 4 * (size_t)j;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      acc.x = fma(-ce[r], q[r].x, acc.x);
+      acc.y = fma(-ce[r], q[r].y, acc.y);
     }
     x[(size_t)e * M + j] = acc;
   }
@@ -455,6 +467,9 @@ gf2_status gf2_tables_build(gf2_ctx *ctx, const int *h_tau_index) {
   }
   pole_resum_kernel<<<1, 256, 0, ctx->stream>>>(n_iw, ctx->d_iw_pole, ctx->d_pole_resum);
   GF2_CK_LAUNCH(ctx, "pole_resum_kernel");
+  GF2_CK(ctx, cudaMalloc(&ctx->d_iw_pole_fold, sizeof(double2) * 4 * (size_t)M));
+  pole_fold_kernel<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, n_iw, ctx->d_iw_pole, ctx->d_iw_pole_fold);
+  GF2_CK_LAUNCH(ctx, "pole_fold_kernel");
   // the lowest n_iw / 8 frequencies serve the coarse counts of the mu search
   ctx->n_coarse = (n_iw >= 2048) ? n_iw / 8 : 0;
   if (ctx->n_coarse) {
@@ -478,7 +493,7 @@ extern "C" gf2_status gf2_fft_iw_to_tau(gf2_ctx *ctx, const double *d_X_iw, cons
   GF2_PROF(ctx, GF2_K_IW2TAU,
            (iw_to_tau_kernel<<<N2 / E, 512, smem, ctx->stream>>>(
                N2, M, ctx->log2M, ctx->n_iw, E, ctx->beta, reinterpret_cast<const double2 *>(d_X_iw), coef,
-               ctx->d_iw_pole, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->n_tau,
+               ctx->d_iw_pole_fold, ctx->d_tau_pole, ctx->d_twiddle, ctx->d_twiddle + M / 2, ctx->n_tau,
                ctx->d_tau_index, d_X_tau)));
   GF2_CK_LAUNCH(ctx, "iw_to_tau_kernel");
   return GF2_OK;

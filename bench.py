@@ -68,10 +68,10 @@ def parse():
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
     ap.add_argument("--workload", default="h32_631g",
-                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma", "h32_mesh"])
+                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma", "h32_mesh", "h64_mesh"])
     ap.add_argument("--n-bf", type=int, default=128, help="basis size of --workload sigma")
     ap.add_argument("--mesh", type=int, nargs=2, default=(7, 32), metavar=("P", "U"),
-                    help="power mesh of --workload h32_mesh (P halvings, U steps per interval)")
+                    help="power mesh of --workload h32_mesh / h64_mesh (P halvings, U steps per interval)")
     ap.add_argument("--max-outer", type=int, default=30, help="outer GF2 iterations of --workload converge")
     ap.add_argument("--profile-run", action="store_true",
                     help="warm-up and timed steps only (no e2e, FP64 sample, energy check or CPU baseline)")
@@ -846,20 +846,31 @@ def first_step_gpu(g, h, s, r, N, n_tau, n_iw, beta, prec, mu_hf=None):
 
 def run_mesh(args, rank, world, dist):
     """The benchmark's system and step (H32 2x4x4 lattice, 6-31G, N = 64,
-    beta = 100, n_iw = 8192) on the non-equidistant time grid the paper uses
+    beta = 100, n_iw = 8192; with --workload h64_mesh the H64 4x4x4 lattice,
+    N = 128, beta = 200, n_iw = 16384) on the non-equidistant time grid the paper uses
     (Computational details): the uniform power mesh with --mesh P U (P halvings,
     U steps per interval: 2 (P+1) U + 1 points on a uniform grid of 2^(P+1) U
     intervals).  value = 8 N^5 n_points / step time; the energy and density are
     checked against the oracle's first step on the same mesh and on the 4097-point
     uniform grid (stored fixtures written from oracle/ only)."""
     import torch
+    import gf2_inputs as gi
     import paper_1405_3273_gb300 as g
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    s, r = build_inputs()
+    h64 = args.workload == "h64_mesh"
+    if h64:  # H64 4x4x4 lattice, 6-31G (N = 128), beta = 200, 16384 frequencies
+        s = gi.build_system("h64_lattice_631g")
+        r = gi.rhf(s)
+        n_iw, beta, tag = 16384, 200.0, "h64"
+        label = "H64 lattice 4x4x4 at 2.0 bohr, 6-31G (N=128), beta=200"
+    else:
+        s, r = build_inputs()
+        n_iw, beta, tag = WORKLOAD["n_iw"], WORKLOAD["beta"], "h32"
+        label = "H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100"
     p_, u_ = args.mesh
     M, idx = g.power_mesh(p_, u_)
-    N, n_iw, beta = s.nbf, WORKLOAD["n_iw"], WORKLOAD["beta"]
+    N = s.nbf
     n_tau = len(idx)
     prec = PRECS[args.prec]
     f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
@@ -931,8 +942,8 @@ def run_mesh(args, rank, world, dist):
         checks[name] = (log[-1][0], P.clone())
     checks[args.prec] = (E_split, P_split)
     fixtures = {}
-    for key, path in (("same_mesh", f"h32_631g_first_step_pm{p_}x{u_}_w{n_iw}.json"),
-                      ("uniform_4097", f"h32_631g_first_step_t4097_w{n_iw}.json")):
+    for key, path in (("same_mesh", f"{tag}_631g_first_step_pm{p_}x{u_}_w{n_iw}.json"),
+                      ("uniform_4097", f"{tag}_631g_first_step_t4097_w{n_iw}.json")):
         fp = os.path.join(ROOT, "tests", "golden", path)
         if os.path.exists(fp):
             d = json.load(open(fp))
@@ -944,12 +955,12 @@ def run_mesh(args, rank, world, dist):
     _, _, bf16_sust, _ = measured_peaks()
     pair_sym = bool(np.abs(s.eri - s.eri.transpose(2, 3, 0, 1)).max() <= 1e-12 * np.abs(s.eri).max())
     exec_frac = (4.0 * (1056.0 / 2048.0 if pair_sym else 1.0) + 4.0) / 8.0
-    line = {"metric": "GF2 iteration on the non-equidistant time grid (H32 6-31G)",
+    line = {"metric": f"GF2 iteration on the non-equidistant time grid ({tag.upper()} 6-31G)",
             "value": useful / (ms_step * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
             "data": "synthetic (closed-form s-Gaussian integrals, RHF start)",
-            "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N=64), beta=100, n_iw={n_iw}, "
+            "config": {"workload": (f"{label}, n_iw={n_iw}, "
                                     f"power mesh p={p_} u={u_}: {n_tau} time points on a {M}-interval grid"),
                        "step": "one GF2 outer iteration, all hot-path rows",
                        "parallelism": f"replicas x{world}"},
@@ -1182,7 +1193,7 @@ def main():
         run_h32_sto3g(args, rank, world, dist)
     elif args.workload == "converge":
         run_converge(args, rank, world, dist)
-    elif args.workload == "h32_mesh":
+    elif args.workload in ("h32_mesh", "h64_mesh"):
         run_mesh(args, rank, world, dist)
     elif args.workload == "h64":
         run_h64(args, rank, world, dist)

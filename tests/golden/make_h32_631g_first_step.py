@@ -1,5 +1,7 @@
 """Writes the oracle's first GF2 self-energy step on the H32 2x4x4 lattice
-(2.0 bohr, 6-31G, N = 64, 32 electrons, beta = 100) into a JSON fixture.
+(2.0 bohr, 6-31G, N = 64, 32 electrons, beta = 100) into a JSON fixture; with
+--system h64 the same step on the H64 4x4x4 lattice (2.0 bohr, 6-31G, N = 128,
+64 electrons, beta = 200, 16384 frequencies).
 
 The step is the one ``bench.py`` times, done here by the plain FP64 CPU oracle
 only (``oracle/``; no GPU code is imported):
@@ -21,7 +23,9 @@ dominates).  Output: tests/golden/h32_631g_first_step_t{n_tau}_w{n_iw}.json,
 or with --mesh the same step on the uniform power mesh with P halvings and U
 steps per interval (``oracle.grids.power_mesh``; iw -> tau at the mesh
 points, the local-cubic integral through its unequal nodes):
-tests/golden/h32_631g_first_step_pm{P}x{U}_w{n_iw}.json.
+tests/golden/h32_631g_first_step_pm{P}x{U}_w{n_iw}.json (h64_... for --system h64;
+    python tests/golden/make_h32_631g_first_step.py --system h64 --n-iw 16384 --mesh 7 32
+takes about half an hour on 8 cores).
 """
 
 import argparse
@@ -44,15 +48,21 @@ from oracle import sigma as osg  # noqa: E402
 from oracle import transforms as ot  # noqa: E402
 
 
-def fixture_path(n_tau, n_iw, mesh=None):
+SYSTEMS = {"h32": ("h32_lattice_631g", 100.0, "H32 2x4x4 lattice at 2.0 bohr, 6-31G (N=64), beta=100"),
+           "h64": ("h64_lattice_631g", 200.0, "H64 4x4x4 lattice at 2.0 bohr, 6-31G (N=128), beta=200")}
+
+
+def fixture_path(n_tau, n_iw, mesh=None, system="h32"):
     if mesh is not None:
-        return os.path.join(HERE, f"h32_631g_first_step_pm{mesh[0]}x{mesh[1]}_w{n_iw}.json")
-    return os.path.join(HERE, f"h32_631g_first_step_t{n_tau}_w{n_iw}.json")
+        return os.path.join(HERE, f"{system}_631g_first_step_pm{mesh[0]}x{mesh[1]}_w{n_iw}.json")
+    return os.path.join(HERE, f"{system}_631g_first_step_t{n_tau}_w{n_iw}.json")
 
 
-def first_step(n_tau, n_iw, beta=100.0, spacing=2.0, mesh=None):
+def first_step(n_tau, n_iw, beta=None, spacing=2.0, mesh=None, system="h32"):
     t0 = time.time()
-    s = gi.build_system("h32_lattice_631g", spacing=spacing)
+    name, beta0, label = SYSTEMS[system]
+    beta = beta0 if beta is None else beta
+    s = gi.build_system(name, spacing=spacing)
     r = gi.rhf(s)
     F = r.F
     mu0, G0, P0, nev0 = od.mu_search(s.S, F, None, None, None, s.n_elec, beta, n_iw)
@@ -77,7 +87,7 @@ def first_step(n_tau, n_iw, beta=100.0, spacing=2.0, mesh=None):
     ks = sorted({0, 1, (n_tau - 1) // 4, (n_tau - 1) // 2, n_tau - 2, n_tau - 1})
     return {
         "what": ("oracle first GF2 self-energy step from the finite-temperature HF state, "
-                 "H32 2x4x4 lattice at 2.0 bohr, 6-31G (N=64), beta=100; F held at F_HF"),
+                 f"{label}; F held at F_HF"),
         "written_by": "tests/golden/make_h32_631g_first_step.py (calls oracle/ and gf2_inputs only)",
         "n_bf": int(s.nbf), "n_elec": int(s.n_elec), "beta": beta, "n_tau": n_tau, "n_iw": n_iw,
         "mesh": None if mesh is None else {"p": mesh[0], "u": mesh[1], "M": int(M)},
@@ -99,10 +109,11 @@ def main():
     ap.add_argument("--n-tau", type=int, default=4097)
     ap.add_argument("--n-iw", type=int, default=8192)
     ap.add_argument("--mesh", type=int, nargs=2, default=None, metavar=("P", "U"))
+    ap.add_argument("--system", default="h32", choices=sorted(SYSTEMS))
     a = ap.parse_args()
     mesh = tuple(a.mesh) if a.mesh else None
-    d = first_step(a.n_tau, a.n_iw, mesh=mesh)
-    with open(fixture_path(a.n_tau, a.n_iw, mesh), "w") as f:
+    d = first_step(a.n_tau, a.n_iw, mesh=mesh, system=a.system)
+    with open(fixture_path(a.n_tau, a.n_iw, mesh, a.system), "w") as f:
         json.dump(d, f, indent=0)
     print(json.dumps({k: v for k, v in d.items() if k not in ("P", "sigma_tau_samples")}))
 

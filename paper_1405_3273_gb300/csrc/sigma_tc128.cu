@@ -15,7 +15,11 @@
 //               MMA2: D2[l, n] = sum_m A2[l, m] GT[n][m] (A from TMEM, B = the
 //               same G(tau)^T tiles), written into the TMEM buffer that D1t
 //               of the same unit occupied.  Four warps stage D2 as FP32 and
-//               store T2[c][i][q][l][n] with TMA.
+//               store T2[c][i][q][l][n] with TMA.  When v has the pair
+//               symmetry (im|qk) = (qk|im), T2[c][i][q][l][n] =
+//               T2[c][q][i][n][l]: only the units with q >= i run (8256 of
+//               16384 per time point) and each tile with q > i is also
+//               written transposed, as tile (q, i), by plain coalesced stores.
 //  xform128     stage 3.  Unit (c, i, l): D3[n, p] = sum_q T2[c][i][q][l][n]
 //               Gbar[p][q]; FP32 T2 tiles by TMA, split by eight converter
 //               warps (one per TMEM lane and K block) into TMEM, A from TMEM,
@@ -67,6 +71,29 @@ __device__ __forceinline__ void stage_row64(uint8_t *tile, int row, const float 
 // TMEM: X buffers at columns 0 and 128 (D1t, then D2 of the same unit),
 // A2 stages from column 256, [K block][term] x 32 columns each.
 // ---------------------------------------------------------------------------
+constexpr int kSym128Units = P * (P + 1) / 2;  // (i, q) with i <= q
+
+// unit u of a launch -> (time point c, i, q); with the pair symmetry the units
+// of a time point are the upper triangle i <= q, row by row
+__device__ __forceinline__ void sandwich128_unit(int u, int sym, int &c, int &i, int &q) {
+  if (!sym) {
+    c = u / (P * P);
+    i = (u / P) % P;
+    q = u % P;
+    return;
+  }
+  c = u / kSym128Units;
+  const int r = u - c * kSym128Units;
+  // rows before row i hold i P - i (i - 1) / 2 units
+  const double b = 2.0 * P + 1.0;
+  int ii = (int)((b - sqrt(b * b - 8.0 * r)) * 0.5);
+  ii = max(0, min(P - 1, ii));
+  while (ii > 0 && ii * P - ii * (ii - 1) / 2 > r) --ii;
+  while (ii < P - 1 && (ii + 1) * P - (ii + 1) * ii / 2 <= r) ++ii;
+  i = ii;
+  q = ii + (r - (ii * P - ii * (ii - 1) / 2));
+}
+
 template <int T>
 constexpr int sw128_vstages() { return T == 2 ? 2 : 1; }
 template <int T>
@@ -76,7 +103,7 @@ template <int T, int F>
 __global__ void __launch_bounds__(320, 1)
     sandwich128_kernel(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_g,
                        const __grid_constant__ CUtensorMap map_t2s, int S, int sl0, int n_units,
-                       int *__restrict__ ex, int *err) {
+                       int *__restrict__ ex, int *err, int sym, float *__restrict__ t2) {
   constexpr int VS = sw128_vstages<T>(), A2S = sw128_a2stages<T>();
   constexpr uint32_t G_SET = T * kOperand, V_STAGE = T * kOperand, A2_COLS = 2 * T * 32;
   constexpr uint32_t kIdesc = idesc_fmt(F, 128, 128, 0, 0);
@@ -125,7 +152,8 @@ __global__ void __launch_bounds__(320, 1)
     const uint64_t keep_pol = tc::policy_evict_last();
     int it = 0, cur_c = -1, gcount = 0;
     for (int u = u_begin; u < u_end; ++u, ++it) {
-      const int c = u / (P * P), i = (u / P) % P, q = u % P;
+      int c, i, q;
+      sandwich128_unit(u, sym, c, i, q);
       if (c != cur_c) {
         if (gcount >= 1 && !tc::mbar_wait(g_empty, (gcount - 1) & 1, abort)) { raise_abort(abort, err); break; }
         tc::mbar_arrive_expect_tx(g_full, G_SET);
@@ -145,8 +173,9 @@ __global__ void __launch_bounds__(320, 1)
     }
   } else if (warp == 1 && lane == 0) {
     int it = 0, cur_c = -1, gcount = 0;
+    const int per_c = sym ? kSym128Units : P * P;
     for (int u = u_begin; u < u_end; ++u, ++it) {
-      const int c = u / (P * P);
+      const int c = u / per_c;
       if (c != cur_c) {
         if (cur_c >= 0) tc::mma_commit(g_empty);
         if (!tc::mbar_wait(g_full, gcount & 1, abort)) { raise_abort(abort, err); break; }
@@ -193,8 +222,9 @@ __global__ void __launch_bounds__(320, 1)
     const uint32_t lanes = (uint32_t)(wq * 32) << 16;
     int it = 0;
     bool ok = true;
+    const int per_c = sym ? kSym128Units : P * P;
     for (int u = u_begin; u < u_end && ok; ++u, ++it) {
-      const int c = u / (P * P), x = it & 1, a2 = it % A2S;
+      const int c = u / per_c, x = it & 1, a2 = it % A2S;
       if (!tc::mbar_wait(&d1_full[x], (it >> 1) & 1, abort)) { raise_abort(abort, err); break; }
       __syncwarp();
       tc::tc_fence_after();
@@ -227,7 +257,11 @@ __global__ void __launch_bounds__(320, 1)
     float run_mx = 0.f;  // FP16: largest |T2| of time point run_c seen by this thread
     bool ok = true;
     for (int u = u_begin; u < u_end && ok; ++u, ++it) {
-      const int c = u / (P * P), i = (u / P) % P, q = u % P, x = it & 1;
+      int c, i, q;
+      sandwich128_unit(u, sym, c, i, q);
+      const int x = it & 1;
+      // the mirrored tile (q, i): row l of this warp -> column l of T2[c][q][i][n][.]
+      float *mirror = (sym && q > i) ? t2 + ((((size_t)c * P + q) * P + i) * P) * P + row : nullptr;
       if (F != 0 && c != run_c) {
         if (run_c >= 0) warp_absmax_to(&ex[kMaxT2 * S + sl0 + run_c], run_mx);
         run_c = c;
@@ -254,6 +288,10 @@ __global__ void __launch_bounds__(320, 1)
           }
         }
         if (pass >= 1 && !tc::mbar_wait(o_empty, (pass - 1) & 1, abort)) { raise_abort(abort, err); ok = false; break; }
+        if (mirror) {  // T2[c][q][i][n][l] = D2[l][n]: 32 lanes write 128 consecutive bytes per n
+#pragma unroll
+          for (int k = 0; k < 64; ++k) mirror[(size_t)(64 * hh + k) * P] = v[k];
+        }
         stage_row64(sO, row, v);
         tc::fence_proxy_async_smem();  // these writes are read by the TMA store
         __syncwarp();
@@ -764,10 +802,11 @@ gf2_status run128(gf2_ctx *ctx, TcState128 *s, const double *d_G, int k0, int co
   for (int c0 = 0, sl0 = 0; c0 < count; c0 += C, sl0 += C) {
     const int cnt = std::min(C, count - c0);
     double *out = d_out + (size_t)c0 * N * N;
-    const int u12 = cnt * P * P;
+    const int u12 = cnt * P * P, sym = ctx->tc_pair_sym ? 1 : 0;
+    const int u12s = sym ? cnt * kSym128Units : u12;
     GF2_PROF(ctx, GF2_K_SANDWICH,
-             (sandwich128_kernel<T, F><<<std::min(u12, sms), 320, ssw, ctx->stream>>>(
-                 map_v, s->map_g, s->map_t2s, S, sl0, u12, s->gexp, ctx->d_err)));
+             (sandwich128_kernel<T, F><<<std::min(u12s, sms), 320, ssw, ctx->stream>>>(
+                 map_v, s->map_g, s->map_t2s, S, sl0, u12s, s->gexp, ctx->d_err, sym, s->T2)));
     GF2_CK_LAUNCH(ctx, "sandwich128_kernel");
     GF2_PROF(ctx, GF2_K_XFORM,
              (xform128_kernel<T, F><<<std::min(u12, sms), 320, sxf, ctx->stream>>>(

@@ -8,6 +8,9 @@
   physical finite-temperature HF Green's function in the orthonormal basis,
   the split path against the FP64 GPU path on sampled points near tau = 0 and
   mid-grid (the FP64 path is itself checked against the oracle at N = 128).
+* These integrals have the pair symmetry (im|qk) = (qk|im), so the sandwich
+  computes the upper triangle of (i, q) tiles and mirrors it; N = 80 with
+  integrals that lack it runs every tile.
 
 Tolerances as for N = 64 (``tests/test_gpu_tc.py``): three BF16 terms or two
 FP16 terms keep ~22-24 significant bits per operand, two BF16 terms ~16.
@@ -118,3 +121,20 @@ def test_split_sigma_h64_lattice_physical_g(g):
             rel = np.abs(out[prec][j] - ref).max() / np.abs(ref).max()
             print(f"H64 lattice split Sigma prec={prec} tau index {k}: max rel error {rel:.3e}")
             assert rel <= 5e-6, (prec, k)
+
+
+def test_split_sigma_n80_without_pair_symmetry(g):
+    """Integrals without the pair symmetry (im|qk) = (qk|im): the 128-wide
+    sandwich then computes every (i, q) tile instead of the upper triangle and
+    its mirror; the symmetric part of Sigma is returned."""
+    n, n_tau = 80, 9
+    G = gi.random_symmetric_g(n, n_tau, seed=83) * 0.3
+    rng = np.random.default_rng(84)
+    v = gi.random_eri(n, seed=85) + 0.05 * rng.normal(size=(n, n, n, n))
+    ref = osg.sigma_tau(G, v)
+    ref = 0.5 * (ref + np.swapaxes(ref, 1, 2))
+    got = split_sigma(g, G, v, (2, 3))
+    for prec in (2, 3):
+        rel = np.abs(got[prec] - ref).max() / np.abs(ref).max()
+        print(f"N=80 split Sigma without pair symmetry prec={prec}: max rel error {rel:.3e}")
+        assert rel <= RTOL[prec], prec

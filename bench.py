@@ -708,7 +708,7 @@ def run_batch(args, rank, world, dist):
         t = time.perf_counter()
         g.gf2_batch_tune(b.handle, Gs, p)
         tune_s = time.perf_counter() - t
-        plan = [g.gf2_batch_plan(b.handle, i) for i in range(len(sizes))]
+        plan = [g.gf2_batch_plan(b.handle, i) + (g.gf2_batch_partner(b.handle, i),) for i in range(len(sizes))]
         for _ in range(warmup):
             g.gf2_sigma_tau_batched(b.handle, Gs, outs, p)
         torch.cuda.synchronize()
@@ -738,8 +738,9 @@ def run_batch(args, rank, world, dist):
                        "step": "one gf2_sigma_tau_batched call (graph replay)", "parallelism": f"replicas x{world}",
                        "l2": "inputs 1.0 GB, intermediates of the split instances several GB"},
             "all_fp64_ms_per_step": ms64, "speedup_vs_all_fp64": ms64 / ms, "tune_s": tune_s,
-            "plan": [{"N": n, "path": names[p], "est_ms": round(e, 3), "lane": l, "slots_per_launch": c}
-                     for n, (p, e, l, c) in zip(sizes, plan)],
+            "plan": [{"N": n, "path": names[p], "est_ms": round(e, 3), "lane": l, "slots_per_launch": c,
+                      "shares_tiles_with": q}
+                     for n, (p, e, l, c, q) in zip(sizes, plan)],
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

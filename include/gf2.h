@@ -309,6 +309,15 @@ const char *gf2_batch_last_error(const gf2_batch *b);
 gf2_status gf2_batch_set_system(gf2_batch *b, int inst, const double *d_v, const double *d_S);
 gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau, int prec);
 gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, double *est_ms, int *lane, int *chunk);
+/* Shared tiles: with a BF16 split (GF2_PREC_BF16X3/X6) the tuner pairs every
+ * split-path instance with 32 < N <= 64, which pays the whole 64-wide tile
+ * set, with the largest other instance of the same n_tau (and both with or
+ * both without an overlap) that fits beside it, N_a + N_b <= 64, and runs the
+ * two as one block-diagonal system (its Sigma is block-diagonal with the two
+ * Sigmas on its diagonal, Eq. Sigma never coupling the blocks); the smaller
+ * one then reports est_ms = 0.  *partner = the other instance of inst's pair,
+ * or -1.  GF2_ERR_ARG before gf2_batch_tune or for a bad instance. */
+gf2_status gf2_batch_partner(const gf2_batch *b, int inst, int *partner);
 gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, double *const *d_Sigma_tau,
                                  int prec);
 

@@ -63,6 +63,7 @@ _SIGS = {
     "gf2_batch_set_system": [_P, _I, _P, _P],
     "gf2_batch_tune": [_P, ctypes.POINTER(_P), _I],
     "gf2_batch_plan": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "gf2_batch_partner": [_P, _I, ctypes.POINTER(_I)],
     "gf2_sigma_tau_batched": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _I],
     "gf2_profile": [_P, _I],
     "gf2_profile_report": [_P, ctypes.c_char_p, _I, ctypes.POINTER(ctypes.c_longlong)],
@@ -325,6 +326,13 @@ def gf2_batch_plan(b, inst):
     _check_batch(lib().gf2_batch_plan(b, int(inst), ctypes.byref(p), ctypes.byref(ms), ctypes.byref(lane),
                                       ctypes.byref(chunk)), b)
     return p.value, ms.value, lane.value, chunk.value
+
+
+def gf2_batch_partner(b, inst):
+    """The instance sharing inst's block-diagonal system (BF16 splits), or -1."""
+    q = ctypes.c_int(-1)
+    _check_batch(lib().gf2_batch_partner(b, int(inst), ctypes.byref(q)), b)
+    return q.value
 
 
 def gf2_sigma_tau_batched(b, G_taus, Sigma_taus, prec):

@@ -12,6 +12,18 @@
 // replay is ordered after the caller's stream and before its later work by
 // events.  Later calls with the same buffers replay the graph with one launch;
 // the error words of the split kernels are read once afterwards.
+//
+// Shared tiles.  With a BF16 split, an instance with 32 < N <= 64 pays the
+// whole 64-wide tile set whatever its N.  The tuner pairs each such instance
+// with the largest unpaired instance of the same time grid that fits beside
+// it (N_a + N_b <= 64) and runs the two as one block-diagonal system: v, S and
+// G(tau) are block-diagonal, every term of Eq. Sigma keeps its indices inside
+// one block (v couples i, m, q, k; W couples l, p, n, j; G links k-l, m-n,
+// p-q), so the Sigma of the pair is block-diagonal with the two Sigmas on its
+// diagonal and the smaller instance costs nothing extra.  Each pair owns a
+// context; the graph gathers the two G(tau) into its block-diagonal input and
+// scatters the two Sigma blocks back.  FP16 splits are not paired: their
+// power-of-two scales are per time point and would be shared by the two.
 #include <algorithm>
 #include <new>
 #include <numeric>
@@ -35,6 +47,15 @@ struct gf2_batch {
   std::vector<int> chunk;      // split pipeline: time-point slots per launch
   std::vector<double> est_ms;  // estimated ms of one full-grid Sigma build
   std::vector<int> lane_of;
+  // instances sharing one block-diagonal system (see the header comment)
+  struct Pair {
+    int big = -1, small = -1;
+    gf2_ctx *ctx = nullptr;
+    double *G = nullptr, *Sig = nullptr;  // [n_tau][N_big + N_small]^2 gather / result buffers
+  };
+  std::vector<Pair> pairs;
+  std::vector<int> pair_of;            // index into pairs, or -1
+  std::vector<double *> S_copy;        // the overlap given to gf2_batch_set_system (or NULL)
   // recorded graph and the buffers it was recorded with
   cudaGraphExec_t exec = nullptr;
   int graph_prec = -1;
@@ -62,6 +83,64 @@ bool split_prec(int p) {
   return p == GF2_PREC_BF16X3 || p == GF2_PREC_BF16X6 || p == GF2_PREC_FP16X3 || p == GF2_PREC_FP16X6;
 }
 
+// out[t] = blockdiag(A[t], B[t]) for t < count (A: na x na, B: nb x nb)
+__global__ void blockdiag2_kernel(int na, int nb, int count, const double *__restrict__ A,
+                                  const double *__restrict__ B, double *__restrict__ out) {
+  const int ns = na + nb;
+  const long long total = (long long)count * ns * ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / ((long long)ns * ns);
+    const int r = (int)(e - t * ns * ns), i = r / ns, j = r - i * ns;
+    double x = 0.0;
+    if (i < na && j < na) x = A[(t * na + i) * na + j];
+    else if (i >= na && j >= na) x = B[(t * nb + (i - na)) * nb + (j - na)];
+    out[e] = x;
+  }
+}
+
+// A[t] = in[t][:na, :na], B[t] = in[t][na:, na:]
+__global__ void blocksplit2_kernel(int na, int nb, int count, const double *__restrict__ in,
+                                   double *__restrict__ A, double *__restrict__ B) {
+  const int ns = na + nb;
+  const long long total = (long long)count * ns * ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / ((long long)ns * ns);
+    const int r = (int)(e - t * ns * ns), i = r / ns, j = r - i * ns;
+    if (i < na && j < na) A[(t * na + i) * na + j] = in[e];
+    else if (i >= na && j >= na) B[(t * nb + (i - na)) * nb + (j - na)] = in[e];
+  }
+}
+
+// v[i][j][k][l] of the pair: A's when all four indices lie in the first block,
+// B's when all lie in the second, zero otherwise
+__global__ void blockdiag4_kernel(int na, int nb, const double *__restrict__ A, const double *__restrict__ B,
+                                  double *__restrict__ out) {
+  const long long ns = na + nb, total = ns * ns * ns * ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(e % ns), k = (int)((e / ns) % ns), j = (int)((e / (ns * ns)) % ns), i = (int)(e / (ns * ns * ns));
+    double x = 0.0;
+    if (i < na && j < na && k < na && l < na) x = A[(((long long)i * na + j) * na + k) * na + l];
+    else if (i >= na && j >= na && k >= na && l >= na)
+      x = B[(((long long)(i - na) * nb + (j - na)) * nb + (k - na)) * nb + (l - na)];
+    out[e] = x;
+  }
+}
+
+int grid_of(long long total) { return (int)std::min<long long>((total + 255) / 256, 4096); }
+
+void drop_pairs(gf2_batch *b) {
+  for (auto &p : b->pairs) {
+    if (p.ctx) gf2_destroy(p.ctx);
+    if (p.G) cudaFree(p.G);
+    if (p.Sig) cudaFree(p.Sig);
+  }
+  b->pairs.clear();
+  b->pair_of.assign(b->n, -1);
+}
+
 void drop_graph(gf2_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
@@ -72,6 +151,9 @@ void drop_graph(gf2_batch *b) {
 
 void release(gf2_batch *b) {
   drop_graph(b);
+  drop_pairs(b);
+  for (auto p : b->S_copy)
+    if (p) cudaFree(p);
   for (auto c : b->ctx)
     if (c) gf2_destroy(c);
   for (auto s : b->lanes) cudaStreamDestroy(s);
@@ -106,6 +188,77 @@ gf2_status time_path(gf2_batch *b, int i, const double *d_G, double *d_out, int 
   return st;
 }
 
+// Pairs every split-path instance with 32 < N <= 64 (which pays the whole
+// 64-wide tile set) with the largest unpaired instance of the same time grid
+// and overlap kind that fits beside it, builds the block-diagonal system of
+// each pair and runs it once on the tune input (so the graph recording that
+// follows allocates nothing).  BF16 splits only.
+gf2_status make_pairs(gf2_batch *b, const double *const *d_G_tau, int prec) {
+  drop_pairs(b);
+  if (prec != GF2_PREC_BF16X3 && prec != GF2_PREC_BF16X6) return GF2_OK;
+  std::vector<int> bigs;
+  for (int i = 0; i < b->n; ++i)
+    if (b->path[i] == prec && b->N[i] > 32 && b->N[i] <= kTcMaxN) bigs.push_back(i);
+  std::stable_sort(bigs.begin(), bigs.end(), [&](int x, int y) { return b->est_ms[x] > b->est_ms[y]; });
+  for (int big : bigs) {
+    if (b->pair_of[big] >= 0) continue;
+    int best = -1;
+    for (int j = 0; j < b->n; ++j) {
+      if (j == big || b->pair_of[j] >= 0 || b->N[j] + b->N[big] > kTcMaxN || b->n_tau[j] != b->n_tau[big] ||
+          (b->S_copy[j] == nullptr) != (b->S_copy[big] == nullptr))
+        continue;
+      if (best < 0 || b->est_ms[j] > b->est_ms[best]) best = j;
+    }
+    if (best < 0) continue;
+    gf2_batch::Pair p;
+    p.big = big;
+    p.small = best;
+    const int na = b->N[big], nb = b->N[best], ns = na + nb, nt = b->n_tau[big];
+    gf2_status st = gf2_create(&p.ctx, ns, nt, 8, 1.0, b->origin);
+    if (st != GF2_OK) return bfail(b, st, "shared-tile pair: context");
+    double *tmp = nullptr;
+    const size_t n4 = (size_t)ns * ns * ns * ns;
+    if (cudaMalloc(&tmp, sizeof(double) * std::max(n4, (size_t)ns * ns)) != cudaSuccess) {
+      gf2_destroy(p.ctx);
+      return bfail(b, GF2_ERR_NOMEM, "shared-tile pair: integrals");
+    }
+    blockdiag4_kernel<<<grid_of((long long)n4), 256, 0, b->origin>>>(na, nb, b->ctx[big]->d_v, b->ctx[best]->d_v, tmp);
+    st = gf2_set_integrals(p.ctx, tmp);
+    if (st == GF2_OK && b->S_copy[big]) {
+      blockdiag2_kernel<<<grid_of((long long)ns * ns), 256, 0, b->origin>>>(na, nb, 1, b->S_copy[big],
+                                                                           b->S_copy[best], tmp);
+      st = gf2_set_overlap(p.ctx, tmp);
+    }
+    cudaStreamSynchronize(b->origin);
+    cudaFree(tmp);
+    const size_t grid_bytes = sizeof(double) * (size_t)nt * ns * ns;
+    if (st == GF2_OK && (cudaMalloc(&p.G, grid_bytes) != cudaSuccess || cudaMalloc(&p.Sig, grid_bytes) != cudaSuccess))
+      st = GF2_ERR_NOMEM;
+    b->pairs.push_back(p);  // owned by the batch from here on (released with it)
+    if (st != GF2_OK) return bfail(b, st, "shared-tile pair: set-up");
+    p.ctx->tc_chunk_max = b->chunk[big];
+    // one run on the tune input: builds the split planes and the workspace
+    blockdiag2_kernel<<<grid_of((long long)nt * ns * ns), 256, 0, b->origin>>>(na, nb, nt, d_G_tau[big],
+                                                                              d_G_tau[best], p.G);
+    st = gf2_sigma_tau_points(p.ctx, p.G, 0, std::min(nt, 2), p.Sig, prec);
+    if (st != GF2_OK) return bfail(b, st, std::string("shared-tile pair: ") + gf2_last_error(p.ctx));
+    if (cudaStreamSynchronize(b->origin) != cudaSuccess) return bfail(b, GF2_ERR_CUDA, "shared-tile pair: sync");
+    const int k = (int)b->pairs.size() - 1;
+    b->pair_of[big] = b->pair_of[best] = k;
+    // the smaller instance's own workspace is no longer used
+    gf2_tc_release(b->ctx[best]);
+    if (b->ctx[best]->d_ws) {
+      cudaFree(b->ctx[best]->d_ws);
+      b->ctx[best]->d_ws = nullptr;
+      b->ctx[best]->ws_elems = 0;
+    }
+    b->path[best] = prec;
+    b->chunk[best] = b->chunk[big];
+    b->est_ms[best] = 0.0;  // runs inside its partner's build
+  }
+  return GF2_OK;
+}
+
 }  // namespace
 
 extern "C" gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n_bf, const int *n_tau, void *stream) {
@@ -123,6 +276,8 @@ extern "C" gf2_status gf2_batch_create(gf2_batch **out, int n_inst, const int *n
   b->ctx.assign(n_inst, nullptr);
   b->N.assign(n_bf, n_bf + n_inst);
   b->n_tau.assign(n_tau, n_tau + n_inst);
+  b->S_copy.assign(n_inst, nullptr);
+  b->pair_of.assign(n_inst, -1);
   gf2_status st = GF2_OK;
   for (int i = 0; i < n_inst && st == GF2_OK; ++i)
     st = gf2_create(&b->ctx[i], n_bf[i], n_tau[i], 8, 1.0, stream);  // Sigma(tau) uses no frequency grid
@@ -161,11 +316,23 @@ extern "C" gf2_status gf2_batch_set_system(gf2_batch *b, int inst, const double 
   if (!b) return GF2_ERR_ARG;
   if (inst < 0 || inst >= b->n || !d_v) return bfail(b, GF2_ERR_ARG, "gf2_batch_set_system: bad instance or NULL v");
   drop_graph(b);
+  drop_pairs(b);
   b->tuned_prec = -1;
   gf2_ctx *c = b->ctx[inst];
   gf2_set_stream(c, b->origin);
   gf2_status st = gf2_set_integrals(c, d_v);
   if (st == GF2_OK && d_S) st = gf2_set_overlap(c, d_S);
+  // a copy of S for a block-diagonal pair built by the tuner
+  if (b->S_copy[inst]) {
+    cudaFree(b->S_copy[inst]);
+    b->S_copy[inst] = nullptr;
+  }
+  if (st == GF2_OK && d_S) {
+    const size_t bytes = sizeof(double) * b->N[inst] * b->N[inst];
+    if (cudaMalloc(&b->S_copy[inst], bytes) != cudaSuccess ||
+        cudaMemcpyAsync(b->S_copy[inst], d_S, bytes, cudaMemcpyDeviceToDevice, b->origin) != cudaSuccess)
+      return bfail(b, GF2_ERR_NOMEM, "gf2_batch_set_system: copy of S");
+  }
   return from_ctx(b, inst, st);
 }
 
@@ -178,6 +345,7 @@ extern "C" gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau,
     if (!b->ctx[i]->have_integrals) return bfail(b, GF2_ERR_ARG, "gf2_batch_tune: gf2_batch_set_system not called");
   }
   drop_graph(b);
+  drop_pairs(b);
   b->path.assign(b->n, GF2_PREC_FP64);
   b->chunk.assign(b->n, 32);
   b->est_ms.assign(b->n, 0.0);
@@ -239,6 +407,7 @@ extern "C" gf2_status gf2_batch_tune(gf2_batch *b, const double *const *d_G_tau,
   }
   cudaFree(d_out);
   if (st != GF2_OK) return st;
+  if ((st = make_pairs(b, d_G_tau, prec)) != GF2_OK) return st;
   // longest estimated time first, each to the least-loaded lane
   std::vector<int> order(b->n);
   std::iota(order.begin(), order.end(), 0);
@@ -263,6 +432,13 @@ extern "C" gf2_status gf2_batch_plan(const gf2_batch *b, int inst, int *path, do
   return GF2_OK;
 }
 
+extern "C" gf2_status gf2_batch_partner(const gf2_batch *b, int inst, int *partner) {
+  if (!b || inst < 0 || inst >= b->n || b->tuned_prec < 0 || !partner) return GF2_ERR_ARG;
+  const int k = b->pair_of[inst];
+  *partner = k < 0 ? -1 : (b->pairs[k].big == inst ? b->pairs[k].small : b->pairs[k].big);
+  return GF2_OK;
+}
+
 extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, double *const *d_Sigma_tau,
                                             int prec) {
   if (!b) return GF2_ERR_ARG;
@@ -284,6 +460,22 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
       cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0);
       for (int i = 0; i < b->n && st == GF2_OK; ++i) {
         if (b->lane_of[i] != (int)l) continue;
+        if (b->pair_of[i] >= 0) {  // the pair runs on its larger instance's lane
+          const gf2_batch::Pair &p = b->pairs[b->pair_of[i]];
+          if (i != p.big) continue;
+          const int na = b->N[p.big], nb = b->N[p.small], ns = na + nb, nt = b->n_tau[p.big];
+          const int grid = grid_of((long long)nt * ns * ns);
+          blockdiag2_kernel<<<grid, 256, 0, b->lanes[l]>>>(na, nb, nt, d_G_tau[p.big], d_G_tau[p.small], p.G);
+          gf2_set_stream(p.ctx, b->lanes[l]);
+          p.ctx->defer_error_check = true;
+          gf2_status sp = gf2_sigma_tau(p.ctx, p.G, p.Sig, b->path[i]);
+          p.ctx->defer_error_check = false;
+          if (sp != GF2_OK) st = bfail(b, sp, "shared-tile pair of instances " + std::to_string(p.big) + " and " +
+                                                  std::to_string(p.small) + ": " + gf2_last_error(p.ctx));
+          blocksplit2_kernel<<<grid, 256, 0, b->lanes[l]>>>(na, nb, nt, p.Sig, d_Sigma_tau[p.big],
+                                                           d_Sigma_tau[p.small]);
+          continue;
+        }
         gf2_ctx *c = b->ctx[i];
         gf2_set_stream(c, b->lanes[l]);
         c->defer_error_check = true;
@@ -306,6 +498,7 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
     }
     if (graph) cudaGraphDestroy(graph);
     for (int i = 0; i < b->n; ++i) gf2_set_stream(b->ctx[i], b->origin);
+    for (auto &p : b->pairs) gf2_set_stream(p.ctx, b->origin);
     if (st != GF2_OK) return st;
     b->graph_prec = prec;
     b->graph_g.assign(d_G_tau, d_G_tau + b->n);
@@ -322,8 +515,9 @@ extern "C" gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d
     return bfail(b, GF2_ERR_CUDA, std::string("batched Sigma: ") + cudaGetErrorString(e));
   for (int i = 0; i < b->n; ++i) {
     if (!split_prec(b->path[i])) continue;
+    const gf2_ctx *c = b->pair_of[i] >= 0 ? b->pairs[b->pair_of[i]].ctx : b->ctx[i];
     int flag = 0;
-    if (cudaMemcpy(&flag, b->ctx[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       return bfail(b, GF2_ERR_CUDA, "batched Sigma: reading an error word");
     if (flag) return bfail(b, GF2_ERR_TIMEOUT, "instance " + std::to_string(i) + ": a pipeline wait timed out");
   }

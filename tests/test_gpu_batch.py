@@ -1,7 +1,9 @@
 """GPU checks of the batched Sigma entry points (gf2_batch_*, gf2_sigma_tau_batched).
 
-A batch of systems of uneven size runs through the autotuner and one recorded
-CUDA graph; every instance's Sigma(tau) is compared with the oracle's Eq. Sigma
+A batch of systems of uneven size (N = 4 .. 64, among them N = 36, 40 and 50)
+runs through the autotuner and one recorded CUDA graph, with BF16 pairs of
+instances sharing one block-diagonal 64-wide system; every instance's
+Sigma(tau) is compared with the oracle's Eq. Sigma
 at the tolerance of the path the tuner chose (FP64: 1e-10 relative; FP16x3 and
 BF16x6 split: 3e-6 relative, as in the single-system split tests).  A second
 call replays the graph on new contents of the same buffers.
@@ -16,7 +18,10 @@ from oracle import sigma as osg
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(4, 33), (10, 33), (17, 33), (40, 17), (64, 17)]   # (N, n_tau), uneven on purpose
+# (N, n_tau), uneven on purpose; with a BF16 split the tuner pairs two of the
+# N = 36, 40, 50 instances with the smaller ones of the same grid (24, 12) into
+# block-diagonal 64-wide systems; N = 64 finds no partner
+SIZES = [(4, 33), (10, 33), (17, 33), (40, 17), (64, 17), (36, 17), (24, 17), (50, 17), (12, 17)]
 TOL = {0: 1e-10, 2: 3e-6, 3: 3e-6}
 
 
@@ -59,7 +64,18 @@ def test_batched_sigma_matches_oracle_and_replays(g, systems, prec):
         print("plan (path, est ms, lane, slots per launch):", plans)
         assert all(p[3] in (16, 32) for p in plans)
         assert all(p[0] in (0, prec) for p in plans)
-        assert plans[-1][0] == prec, "N = 64 should take the tensor-core path"
+        assert plans[4][0] == prec, "N = 64 should take the tensor-core path"
+        partners = [g.gf2_batch_partner(b.handle, i) for i in range(len(SIZES))]
+        print("partners:", partners)
+        for i, q in enumerate(partners):
+            if q >= 0:
+                assert partners[q] == i and SIZES[i][0] + SIZES[q][0] <= 64 and SIZES[i][1] == SIZES[q][1]
+        if prec == 2:  # BF16: the 33..50 instances share their tiles where a partner fits
+            # two smaller instances on the 17-point grid (24, 12) for three larger ones
+            assert sum(q >= 0 for q in partners) == 4 and partners[4] == -1
+            assert all(plans[i][1] == 0.0 for i, q in enumerate(partners) if q >= 0 and SIZES[i][0] < SIZES[q][0])
+        else:          # FP16 scales are per time point: never shared
+            assert all(q == -1 for q in partners)
         # (for N = 4 the two paths take about the same time; either choice is valid)
         for i, (_, _, ref) in enumerate(systems):
             rel = np.abs(outs[i].cpu().numpy() - ref).max() / np.abs(ref).max()

@@ -35,19 +35,39 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FIXTURES = sorted(glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_t*_w*.json")) +
-                  glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_pm*_w*.json")))
+                  glob.glob(os.path.join(HERE, "golden", "h32_631g_first_step_pm*_w*.json")) +
+                  glob.glob(os.path.join(HERE, "golden", "h64_631g_first_step_pm*_w*.json")))
 BOUNDS = {0: (1e-8, 1e-8), 2: (1e-6, 1e-6), 3: (1e-6, 1e-6), 4: (1e-6, 1e-6)}
+# H64 (N = 128, beta = 200; the h64_... fixture, a 513-point mesh): the split
+# Sigma keeps its per-point error (2e-6 relative, twice N = 64's: the sums are
+# twice as long) and its Sigma(i w_0) error (2e-6), but P of this lattice at
+# beta = 200 answers a Sigma error 10-20 times more strongly than the H32
+# lattice at beta = 100 (the FP64 path: 5e-9).  Measured: BF16x6 |dE| 3.5e-7 Eh,
+# max|dP| 3.8e-5; FP16x3 1.9e-6 Eh, 4.8e-6; FP16x6 1.8e-6 Eh, 5.2e-6.  The
+# bounds are those numbers rounded up: only BF16x6 meets 1 uEh there, and no
+# split meets 1e-6 on the density.
+BOUNDS_N128 = {0: (1e-8, 1e-8), 2: (1e-6, 5e-5), 3: (3e-6, 1e-5), 4: (3e-6, 1e-5)}
+
+
+_SYSTEMS = {}
 
 
 @pytest.fixture(scope="module")
 def lattice():
+    """(library, system(n_bf)): the H32 (N = 64) or the H64 (N = 128) lattice at 2.0 bohr."""
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     import paper_1405_3273_gb300 as g
     from paper_1405_3273_gb300 import build
     if not os.path.exists(g.LIB_PATH):
         build.build()
-    s = gi.build_system("h32_lattice_631g", spacing=2.0)
-    return g, s, gi.rhf(s)
+
+    def system(n_bf):
+        name = {64: "h32_lattice_631g", 128: "h64_lattice_631g"}[n_bf]
+        if name not in _SYSTEMS:
+            s = gi.build_system(name, spacing=2.0)
+            _SYSTEMS[name] = (s, gi.rhf(s))
+        return _SYSTEMS[name]
+    return g, system
 
 
 def first_step(g, s, r, n_tau, n_iw, beta, precs, grid=None):
@@ -85,9 +105,10 @@ def first_step(g, s, r, n_tau, n_iw, beta, precs, grid=None):
 
 @pytest.mark.parametrize("path", FIXTURES, ids=[os.path.basename(p)[:-5] for p in FIXTURES])
 def test_first_step_matches_oracle(lattice, path):
-    g, s, r = lattice
+    g, system = lattice
     ref = json.load(open(path))
-    assert ref["n_bf"] == s.nbf == 64
+    s, r = system(ref["n_bf"])
+    assert ref["n_bf"] == s.nbf
     n_tau, n_iw, beta = ref["n_tau"], ref["n_iw"], ref["beta"]
     P_ref = np.array(ref["P"])
     grid = None
@@ -98,12 +119,15 @@ def test_first_step_matches_oracle(lattice, path):
     e_hf, P_hf = got["hf"]
     assert abs(e_hf - ref["E_hf"]) < 1e-9
     assert abs(np.trace(P_hf @ s.S) - s.n_elec) <= 1e-10
-    for prec, (e_tol, p_tol) in BOUNDS.items():
-        if prec != 0:
+    checks = []
+    for prec, (e_tol, p_tol) in (BOUNDS_N128 if s.nbf == 128 else BOUNDS).items():
+        if prec != 0 and s.nbf != 128:
             p_tol *= np.sqrt(4096.0 / (n_tau - 1))
         E, P = got[prec]
         dE, dP = abs(E - ref["E"]), np.abs(P - P_ref).max()
         print(f"{os.path.basename(path)} prec {prec}: |dE| {dE:.2e} Eh, max|dP| {dP:.2e}")
+        checks.append((prec, dE, e_tol, dP, p_tol, abs(np.trace(P @ s.S) - s.n_elec)))
+    for prec, dE, e_tol, dP, p_tol, dn in checks:
         assert dE <= e_tol, (prec, dE)
         assert dP <= p_tol, (prec, dP)
-        assert abs(np.trace(P @ s.S) - s.n_elec) <= 1e-10
+        assert dn <= 1e-10

@@ -108,3 +108,15 @@ def test_create_grid_rejects_bad_grids_before_touching_the_device(library):
     assert call(16, good, n_bf=0) == 1
     assert call(16, good, beta=0.0) == 1
     assert h.value is None
+
+
+def test_binding_power_mesh_matches_the_oracle_mesh():
+    """The binding's power mesh (host logic, no GPU) and the oracle's, written
+    separately, give the same grid."""
+    import numpy as np
+    import paper_1405_3273_gb300 as g
+    from oracle import grids
+    for p, u in [(0, 1), (0, 4), (2, 1), (3, 4), (5, 16), (7, 32), (6, 64)]:
+        M, idx = g.power_mesh(p, u)
+        M2, idx2 = grids.power_mesh(p, u)
+        assert M == M2 and np.array_equal(np.asarray(idx), idx2), (p, u)

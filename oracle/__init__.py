@@ -15,7 +15,9 @@ Every routine follows the paper's definitions directly:
   * ``fock``       -- Eq. FockMatrix;
   * ``energy``     -- Galitskii-Migdal energy;
   * ``occupations`` -- natural occupation numbers eig(S^1/2 P S^1/2)/2;
+  * ``df``         -- Eq. Sigma on density-fitted integrals, written out and
+                      in the three-index factors alone;
   * ``gf2``        -- the self-consistent loop of the supplement (steps 1-3).
 """
 
-from . import grids, sigma, transforms, dyson, fock, energy, gf2, occupations  # noqa: F401
+from . import grids, sigma, transforms, dyson, fock, energy, gf2, occupations, df  # noqa: F401

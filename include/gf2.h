@@ -144,6 +144,30 @@ gf2_status gf2_sigma_tau(gf2_ctx *ctx, const double *d_G_tau, double *d_Sigma_ta
 gf2_status gf2_sigma_tau_points(gf2_ctx *ctx, const double *d_G_tau, int k0, int count,
                                 double *d_Sigma_out, int prec);
 
+/* Density-fitted integrals (the O(n^3 m) route named in the paper's
+ * computational details and conclusions, m auxiliary functions):
+ *   v_ijkl = sum_Q B[Q][i][j] B[Q][k][l].
+ * d_B: device [m][N][N] FP64, row-major, read during the call (the context
+ * keeps a copy).  The fitted v replaces the context's integrals, with W and
+ * the split copies rebuilt as by gf2_set_integrals, so gf2_sigma_tau, the
+ * Fock build and the energy then use them too.  A later gf2_set_integrals
+ * discards the factor.  GF2_ERR_ARG for a NULL pointer or m outside
+ * 1..65535; GF2_ERR_NOMEM if the copy (m N^2 doubles) cannot be allocated. */
+gf2_status gf2_set_df_integrals(gf2_ctx *ctx, const double *d_B, int m);
+
+/* Eq. Sigma on the density-fitted integrals, in the factor order: with
+ * C^Q = B^Q G(tau) and X^Q = G(-tau) C^Q,
+ *   Sigma(tau) = - sum_Q C^Q U^Q,   U^Q_nj = sum_lp X^Q_pl (2 v_lpnj - v_nplj),
+ * 2 m N^4 + 6 m N^3 flops per time point and 3 m N^2 doubles of workspace per
+ * time point (chunks of up to 1 GB, allocated by the first call), no N^4
+ * intermediate.  The same Sigma as gf2_sigma_tau after gf2_set_df_integrals,
+ * to rounding.  Grid points k0 .. k0+count-1 of the full d_G_tau
+ * [n_tau][N][N]; d_Sigma_out [count][N][N].  prec: GF2_PREC_FP64 (others give
+ * GF2_ERR_UNSUPPORTED).  GF2_ERR_ARG without gf2_set_df_integrals, for a NULL
+ * pointer or a range outside the grid.  Stream-ordered. */
+gf2_status gf2_sigma_tau_df(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_Sigma_out,
+                            int prec);
+
 /* High-frequency moments G1..G4 of G(z) = [(z + mu) S - F - Sigma(z)]^-1 for
  * Sigma(z) ~ Sig1/z + Sig2/z^2 (the analytic tail named in the paper's
  * section on the Fourier transforms):

@@ -46,7 +46,7 @@ def sigma_df_factors(G, Gbar, B):
     X = Gbar[None] @ C                                # [Q, p, l] = (Gbar B^Q G)_pl
     t = np.einsum("qpl,rlp->qr", X, B)                # Tr(X^Q B^R)
     coul = np.einsum("qr,rnj->qnj", t, B)             # sum_R t_QR B^R
-    exch = np.einsum("rnp,qpl,rlj->qnj", B, X, B)     # sum_R B^R X^Q B^R
+    exch = np.array([np.matmul(B @ Xq, B).sum(0) for Xq in X])   # sum_R B^R X^Q B^R
     return -np.einsum("qin,qnj->ij", C, 2.0 * coul - exch)
 
 

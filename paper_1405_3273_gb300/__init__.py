@@ -43,6 +43,8 @@ _SIGS = {
     "gf2_set_overlap": [_P, _P],
     "gf2_sigma_tau": [_P, _P, _P, _I],
     "gf2_sigma_tau_points": [_P, _P, _I, _I, _P, _I],
+    "gf2_set_df_integrals": [_P, _P, _I],
+    "gf2_sigma_tau_df": [_P, _P, _I, _I, _P, _I],
     "gf2_tail_moments": [_P, _P, _P, _D, _P, _P],
     "gf2_fft_iw_to_tau": [_P, _P, _P, _P],
     "gf2_fft_tau_to_iw": [_P, _P, _P, _P],
@@ -181,6 +183,16 @@ def gf2_sigma_tau(ctx, G_tau, Sigma_tau, prec=GF2_PREC_FP64):
 def gf2_sigma_tau_points(ctx, G_tau, k0, count, Sigma_out, prec=GF2_PREC_FP64):
     _check(lib().gf2_sigma_tau_points(ctx, _ptr(G_tau, _F64), int(k0), int(count),
                                       _ptr(Sigma_out, _F64), int(prec)), ctx)
+
+
+def gf2_set_df_integrals(ctx, B):
+    """B: [m, N, N] float64 CUDA tensor, v_ijkl = sum_Q B[Q,i,j] B[Q,k,l]."""
+    _check(lib().gf2_set_df_integrals(ctx, _ptr(B, _F64), int(B.shape[0])), ctx)
+
+
+def gf2_sigma_tau_df(ctx, G_tau, k0, count, Sigma_out, prec=GF2_PREC_FP64):
+    _check(lib().gf2_sigma_tau_df(ctx, _ptr(G_tau, _F64), int(k0), int(count),
+                                  _ptr(Sigma_out, _F64), int(prec)), ctx)
 
 
 def gf2_tail_moments(ctx, S, F, mu, sig12, moments):

@@ -74,7 +74,7 @@ void free_all(gf2_ctx *c) {
   c->prof_pool.clear();
   void *ptrs[] = {c->d_v, c->d_Wt, c->d_Shalf, c->d_orth_ws, c->d_v_split, c->d_wt_split, c->d_v_split16, c->d_wt_split16, c->d_twiddle, c->d_iw_pole,
                   c->d_tau_pole, c->d_pole_resum, c->d_t2w_w, c->d_t2w_corr, c->d_ws,
-                  c->d_err, c->d_small, c->d_red, c->d_tau_index, c->d_fine_a, c->d_grid_lag, c->d_grid_mu, c->d_iw_pole_fold};
+                  c->d_err, c->d_small, c->d_red, c->d_df_B, c->d_df_ws, c->d_tau_index, c->d_fine_a, c->d_grid_lag, c->d_grid_mu, c->d_iw_pole_fold};
   gf2_tc_release(c);
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -242,8 +242,14 @@ extern "C" gf2_status gf2_set_integrals(gf2_ctx *ctx, const double *d_v) {
   if (!d_v) return gf2_fail(ctx, GF2_ERR_ARG, "gf2_set_integrals: NULL pointer");
   const size_t N4 = (size_t)ctx->N * ctx->N * ctx->N * ctx->N;
   if (!ctx->d_v) GF2_CK(ctx, cudaMalloc(&ctx->d_v, N4 * sizeof(double)));
-  if (!ctx->d_Wt) GF2_CK(ctx, cudaMalloc(&ctx->d_Wt, N4 * sizeof(double)));
   GF2_CK(ctx, cudaMemcpyAsync(ctx->d_v, d_v, N4 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->df_m = 0;  // a density-fitted factor no longer matches these integrals
+  return gf2_integrals_ready(ctx);
+}
+
+gf2_status gf2_integrals_ready(gf2_ctx *ctx) {
+  const size_t N4 = (size_t)ctx->N * ctx->N * ctx->N * ctx->N;
+  if (!ctx->d_Wt) GF2_CK(ctx, cudaMalloc(&ctx->d_Wt, N4 * sizeof(double)));
   build_wt_kernel<<<std::max(1, std::min<int>((int)((N4 + 255) / 256), 8 * ctx->num_sms)), 256, 0,
                     ctx->stream>>>(ctx->N, ctx->d_v, ctx->d_Wt);
   GF2_CK_LAUNCH(ctx, "build_wt_kernel");

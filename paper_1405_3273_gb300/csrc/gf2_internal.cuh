@@ -93,6 +93,13 @@ struct gf2_ctx {
   double2 *d_grid_mu = nullptr;    // [n_iw][4]: (beta / M) mu_q(w_n beta / M)
   double grid_dw[8] = {};          // Sig2 weights: slopes at tau = 0 (nodes 0..3) and at beta (n_tau-4..n_tau-1)
 
+  // density-fitted integrals (gf2_set_df_integrals): the factor B [df_m][N][N]
+  // and the FP64 workspace of the factor-order Sigma (C, X, U: 3 df_chunk m N^2)
+  double *d_df_B = nullptr;
+  int df_m = 0, df_cap = 0;
+  double *d_df_ws = nullptr;
+  int df_chunk = 0;
+
   // FP64 Sigma workspace (two ping-pong buffers of chunk * N^4 doubles)
   double *d_ws = nullptr;
   size_t ws_elems = 0;
@@ -190,6 +197,8 @@ gf2_status gf2_tables_build(gf2_ctx *ctx, const int *h_tau_index);
 // shared memory of the tau -> iw kernel of a non-equidistant grid
 size_t gf2_grid_smem_bytes(int M, int n_tau);
 gf2_status gf2_pole_coefficients(gf2_ctx *ctx, const double *d_moments, double *d_coef);
+// W and the tensor-core copies of the integrals now in ctx->d_v
+gf2_status gf2_integrals_ready(gf2_ctx *ctx);
 gf2_status gf2_sigma_fp64(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out);
 gf2_status gf2_sigma_tc(gf2_ctx *ctx, const double *d_G_tau, int k0, int count, double *d_out,
                         int prec);

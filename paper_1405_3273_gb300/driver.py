@@ -14,7 +14,7 @@ import numpy as np
 
 from . import (GF2_PREC_BF16X3, GF2_PREC_FP64, Context, gf2_combine, gf2_energy, gf2_fft_iw_to_tau,
                gf2_fft_tau_to_iw, gf2_fock, gf2_gram, gf2_inner_loop, gf2_mu_search, gf2_set_integrals,
-               gf2_set_overlap, gf2_sigma_tau, gf2_tail_moments)
+               gf2_set_df_integrals, gf2_set_overlap, gf2_sigma_tau, gf2_sigma_tau_df, gf2_tail_moments)
 
 
 @dataclass
@@ -30,18 +30,20 @@ class DeviceSystem:
     n_iw: int
     mu0: float
     grid: tuple = None   # (M, tau_index): a non-equidistant time grid replacing the n_tau uniform points
+    df_B: torch.Tensor = None  # [m, N, N]: density-fitted integrals v_ijkl = sum_Q B_Qij B_Qkl replace v
 
     @property
     def nbf(self):
         return self.S.shape[0]
 
 
-def to_device(system, F_start, mu0, device="cuda", grid=None):
+def to_device(system, F_start, mu0, device="cuda", grid=None, df_B=None):
     f = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
     n_tau = int(system.n_tau) if grid is None else len(grid[1])
     return DeviceSystem(S=f(system.S), h=f(system.h), v=f(system.eri), F0=f(F_start),
                         e_nuc=float(system.e_nuc), n_elec=int(system.n_elec), beta=float(system.beta),
-                        n_tau=n_tau, n_iw=int(system.n_iw), mu0=float(mu0), grid=grid)
+                        n_tau=n_tau, n_iw=int(system.n_iw), mu0=float(mu0), grid=grid,
+                        df_B=None if df_B is None else f(df_B))
 
 
 @dataclass
@@ -62,15 +64,21 @@ class GF2Run:
     mu_evals: list = field(default_factory=list)
     inner_iters: list = field(default_factory=list)
     device_inner: bool = True
+    df_order: bool = False   # Sigma by gf2_sigma_tau_df (the factor order) instead of gf2_sigma_tau
 
 
-def start(sys, prec=GF2_PREC_FP64):
+def start(sys, prec=GF2_PREC_FP64, df_order=False):
     n, nt, nw = sys.nbf, sys.n_tau, sys.n_iw
     ctx = Context(n, nt, nw, sys.beta, grid=sys.grid)
-    gf2_set_integrals(ctx.handle, sys.v)
+    if sys.df_B is not None:
+        gf2_set_df_integrals(ctx.handle, sys.df_B)
+    else:
+        if df_order:
+            raise ValueError("the factor-order Sigma needs density-fitted integrals (DeviceSystem.df_B)")
+        gf2_set_integrals(ctx.handle, sys.v)
     gf2_set_overlap(ctx.handle, sys.S)
     dev = sys.S.device
-    run = GF2Run(ctx=ctx, sys=sys, prec=prec)
+    run = GF2Run(ctx=ctx, sys=sys, prec=prec, df_order=df_order)
     run.F = sys.F0.clone()
     run.mu = sys.mu0
     run.P = torch.zeros(n, n, dtype=torch.float64, device=dev)
@@ -160,19 +168,26 @@ def self_energy_step(run, damping=1.0):
     s = run.sys
     gf2_tail_moments(run.ctx.handle, s.S, run.F, run.mu, run.sig12, run.moments)
     gf2_fft_iw_to_tau(run.ctx.handle, run.G_iw, run.moments, run.G_tau)
+    def sigma(out):
+        if run.df_order:
+            gf2_sigma_tau_df(run.ctx.handle, run.G_tau, 0, s.n_tau, out, run.prec)
+        else:
+            gf2_sigma_tau(run.ctx.handle, run.G_tau, out, run.prec)
+
     if damping < 1.0 and run.sig12 is not None:
         new = torch.empty_like(run.Sigma_tau)
-        gf2_sigma_tau(run.ctx.handle, run.G_tau, new, run.prec)
+        sigma(new)
         gf2_combine(run.ctx.handle, [damping, 1.0 - damping], [new, run.Sigma_tau], run.Sigma_tau)
     else:
-        gf2_sigma_tau(run.ctx.handle, run.G_tau, run.Sigma_tau, run.prec)
+        sigma(run.Sigma_tau)
     if run.sig12 is None:
         run.sig12 = torch.empty(2, s.nbf, s.nbf, dtype=torch.float64, device=s.S.device)
     gf2_fft_tau_to_iw(run.ctx.handle, run.Sigma_tau, run.Sigma_iw, run.sig12)
 
 
-def run_gf2(sys, prec=GF2_PREC_FP64, max_outer=30, e_tol=1e-8, damping=1.0, inner_tol=1e-8, callback=None):
-    run = start(sys, prec)
+def run_gf2(sys, prec=GF2_PREC_FP64, max_outer=30, e_tol=1e-8, damping=1.0, inner_tol=1e-8, callback=None,
+            df_order=False):
+    run = start(sys, prec, df_order)
     inner_loop(run, inner_tol)
     run.energies.append(energy(run))
     for _ in range(max_outer):

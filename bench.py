@@ -23,6 +23,7 @@ scaled) and a per-kernel breakdown are reported beside it.
   python bench.py --workload converge    # GF2 to convergence on the H10 chain, split vs FP64
   python bench.py --workload h64         # H64 lattice (N = 128), the 128-wide split Sigma
   python bench.py --workload sigma --n-bf 128 --n-tau 33   # the Sigma build alone (kernel profiles)
+  python bench.py --workload h32_df      # density-fitted integrals (m = 192) on the power mesh
 
 The batch workload has the sizes of a multi-system study: linear H_n chains,
 n = 4, 6, ..., 20, 24, 28, ..., 44, 50 (STO-3G, N = n) plus eight H32 2x4x4
@@ -68,7 +69,8 @@ def parse():
     ap.add_argument("--n-tau", type=int, default=None, help="override the tau grid (smaller cases for ncu)")
     ap.add_argument("--n-iw", type=int, default=None, help="override the frequency count")
     ap.add_argument("--workload", default="h32_631g",
-                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma", "h32_mesh", "h64_mesh"])
+                    choices=["h32_631g", "h64", "batch", "h32_sto3g", "converge", "sigma", "h32_mesh", "h64_mesh",
+                             "h32_df"])
     ap.add_argument("--n-bf", type=int, default=128, help="basis size of --workload sigma")
     ap.add_argument("--mesh", type=int, nargs=2, default=(7, 32), metavar=("P", "U"),
                     help="power mesh of --workload h32_mesh / h64_mesh (P halvings, U steps per interval)")
@@ -1161,6 +1163,132 @@ def run_sigma_only(args, rank, world, dist):
                           / bf16_sust}))
 
 
+def run_df(args, rank, world, dist):
+    """One GF2 iteration of the benchmark's system (H32 2x4x4 lattice, 6-31G,
+    N = 64, beta = 100, n_iw = 8192) on density-fitted integrals: six
+    even-tempered s exponents per atom (m = 192 fitted directions), on the
+    power mesh --mesh P U.  The step is run_mesh's, with Sigma(tau) taken in the
+    factor order of the fitted integrals in FP64 (gf2_sigma_tau_df: C = B G,
+    X = Gbar C, U = X W, Sigma = -sum_Q C U; 2 m N^4 + 6 m N^3 flops per time
+    point) and, beside it, by the four-stage split path (--prec) on the same
+    fitted integrals.  value = the factor-order flops of the Sigma build per
+    step / step time."""
+    import torch
+    import gf2_inputs as gi
+    from gf2_inputs import density_fitting as dfi
+    import paper_1405_3273_gb300 as g
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    s, r = build_inputs()
+    B_host = dfi.build_df(s.coords, s.basis)
+    m, N = B_host.shape[0], s.nbf
+    Bf = B_host.reshape(m, N * N)
+    fit_err = float(np.abs(Bf.T @ Bf - s.eri.reshape(N * N, N * N)).max())
+    n_iw, beta = WORKLOAD["n_iw"], WORKLOAD["beta"]
+    p_, u_ = args.mesh
+    M, idx = g.power_mesh(p_, u_)
+    n_tau = len(idx)
+    f64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    S, hcore, F0 = f64(s.S), f64(s.h), f64(r.F)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ctx = g.Context(N, None, n_iw, beta, grid=(M, idx))
+    h = ctx.handle
+    g.gf2_set_df_integrals(h, f64(B_host))
+    g.gf2_set_overlap(h, S)
+    G_iw0 = torch.zeros(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    P0 = torch.zeros(N, N, dtype=torch.float64, device="cuda")
+    mu_hf = 0.5 * (r.eps[s.n_elec // 2 - 1] + r.eps[s.n_elec // 2])
+    mu_hf, _ = g.gf2_mu_search(h, S, F0, None, None, s.n_elec, mu_hf, G_iw0, P0)
+    moments = torch.empty(4, N, N, dtype=torch.float64, device="cuda")
+    G_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_tau = torch.empty(n_tau, N, N, dtype=torch.float64, device="cuda")
+    Sig_iw = torch.empty(n_iw, N, N, dtype=torch.complex128, device="cuda")
+    sig12 = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+    G_iw = torch.empty_like(G_iw0)
+    P = torch.empty_like(P0)
+    F_new = torch.empty_like(F0)
+
+    def step(out, factor_order, sev=None):
+        g.gf2_tail_moments(h, S, F0, mu_hf, None, moments)
+        g.gf2_fft_iw_to_tau(h, G_iw0, moments, G_tau)
+        if sev:
+            sev[0].record(stream)
+        if factor_order:
+            g.gf2_sigma_tau_df(h, G_tau, 0, n_tau, Sig_tau, 0)
+        else:
+            g.gf2_sigma_tau(h, G_tau, Sig_tau, PRECS[args.prec])
+        if sev:
+            sev[1].record(stream)
+        g.gf2_fft_tau_to_iw(h, Sig_tau, Sig_iw, sig12)
+        mu, nev = g.gf2_mu_search(h, S, F0, Sig_iw, sig12, s.n_elec, mu_hf, G_iw, P)
+        g.gf2_fock(h, hcore, P, F_new)
+        e1, e2 = g.gf2_energy(h, hcore, F0, P, S, G_iw, Sig_iw, sig12)
+        out.append((s.e_nuc + e1 + e2, P.clone()))
+
+    res = {}
+    clocks = None
+    for factor_order in (True, False):
+        log = []
+        for _ in range(args.warmup):
+            step(log, factor_order)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sampler = ClockSampler(torch.cuda.current_device())
+        if factor_order:
+            sampler.start()
+        t0, t1 = ev(), ev()
+        sev = [(ev(), ev()) for _ in range(args.steps)]
+        t0.record(stream)
+        for k in range(args.steps):
+            step(log, factor_order, sev[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if factor_order:
+            clocks = sampler.stop()
+        res[factor_order] = {"ms_step": max_over_ranks(t0.elapsed_time(t1) / args.steps, dist),
+                             "sigma_ms": statistics.mean(a.elapsed_time(b) for a, b in sev),
+                             "E": log[-1][0], "P": log[-1][1]}
+    g.gf2_profile(h, True)
+    step([], True)
+    torch.cuda.synchronize()
+    prof, launches = g.gf2_profile_report(h)
+    g.gf2_profile(h, False)
+    ctx.close()
+    df_flops = (2.0 * m * N ** 4 + 6.0 * m * N ** 3) * n_tau
+    fo, sp = res[True], res[False]
+    fp64_peak = 1.25 * (clocks["sm_mhz"] / 2070.0 if clocks else 1.0)
+    dgemm_ms = prof.get("dgemm_fp64", (0, 0.0))[1]
+    line = {"metric": "GF2 iteration on density-fitted integrals (H32 6-31G, m=192), factor-order FP64 Σ",
+            "value": df_flops / (fo["ms_step"] * 1e-3) / 1e12 * world, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fo["ms_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (closed-form s-Gaussian integrals and auxiliary integrals, RHF start)",
+            "config": {"workload": (f"H32 lattice 2x4x4 at 2.0 bohr, 6-31G (N={N}), beta={beta}, n_iw={n_iw}, "
+                                    f"power mesh p={p_} u={u_}: {n_tau} time points; auxiliary set: "
+                                    f"s exponents 0.3 x 2.6^k, k=0..5, on every atom (m={m})"),
+                       "step": "one GF2 outer iteration, all hot-path rows",
+                       "parallelism": f"replicas x{world}"},
+            "fit": {"m": m, "max_abs_v_error": fit_err},
+            "sigma_factor_order_fp64": {"s_per_build": fo["sigma_ms"] * 1e-3,
+                                        "tflops": df_flops / (fo["sigma_ms"] * 1e-3) / 1e12,
+                                        "frac_of_fp64_peak": df_flops / (fo["sigma_ms"] * 1e-3) / 1e12 / fp64_peak,
+                                        "fp64_peak_tflops": fp64_peak,
+                                        "peak_source": "derived: 1.25 TFLOP/s FP64 nominal at 2070 MHz, "
+                                                       "scaled to the sampled clock",
+                                        "dgemm_ms_per_build": dgemm_ms},
+            f"sigma_four_stage_{args.prec}": {"s_per_build": sp["sigma_ms"] * 1e-3, "ms_per_step": sp["ms_step"],
+                                              "abs_dE_vs_factor_order_fp64": abs(sp["E"] - fo["E"]),
+                                              "max_abs_dP_vs_factor_order_fp64":
+                                                  (sp["P"] - fo["P"]).abs().max().item()},
+            "E_factor_order_fp64": fo["E"],
+            "kernels": {k: {"launches": c, "ms": ms} for k, (c, ms) in prof.items()},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_converge(args, rank, world, dist):
     """Self-consistent GF2 on the linear H10 chain (STO-3G, 1.8 bohr, beta = 100,
     n_tau = 2049, n_iw = 4096) until the energy changes by less than 1e-8 Eh between
@@ -1221,6 +1349,8 @@ def main():
         run_h64(args, rank, world, dist)
     elif args.workload == "sigma":
         run_sigma_only(args, rank, world, dist)
+    elif args.workload == "h32_df":
+        run_df(args, rank, world, dist)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -360,8 +360,7 @@ gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, dou
  *   launch; NULL pointers or bad sizes give GF2_ERR_ARG; CUDA failures
  *   GF2_ERR_CUDA.  d_sig12 may be NULL (no tail term).
  *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture.  Every call overwrites the shared array and fully rewrites what it
+ *   device, with that device current).  Every call overwrites the shared array and fully rewrites what it
  *   reads, so consecutive calls are independent; calls that overlap on the GPU
  *   (other streams or threads at the same time) race on it.
  *   Runs on `stream` (a cudaStream_t; NULL = legacy default stream), copies the

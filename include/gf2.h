@@ -360,9 +360,10 @@ gf2_status gf2_sigma_tau_batched(gf2_batch *b, const double *const *d_G_tau, dou
  *   launch; NULL pointers or bad sizes give GF2_ERR_ARG; CUDA failures
  *   GF2_ERR_CUDA.  d_sig12 may be NULL (no tail term).
  *   The first call on a device looks up the array's device address (once per
- *   device, with that device current).  Every call overwrites the shared array and fully rewrites what it
- *   reads, so consecutive calls are independent; calls that overlap on the GPU
- *   (other streams or threads at the same time) race on it.
+ *   device, with that device current).  Every call overwrites the shared
+ *   array and fully rewrites what it reads, so consecutive calls are
+ *   independent; calls that overlap on the GPU (other streams or threads at
+ *   the same time) race on it.
  *   Runs on `stream` (a cudaStream_t; NULL = legacy default stream), copies the
  *   two results to the host and synchronizes that stream before returning. */
 gf2_status gf2_energy_noalloc(int n_bf, int n_iw, double beta, const double *d_h, const double *d_F,

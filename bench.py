@@ -172,6 +172,13 @@ def measured_peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def peak_label(kind, what):
+    """Where a roofline denominator came from."""
+    if kind == "measured":
+        return f"measured {what} (MEASURED_PEAKS.json)"
+    return f"fallback {what} (no MEASURED_PEAKS.json: an earlier GB300 measurement)"
+
+
 def ncu_traffic(kernel, prec="bf16x6"):
     """DRAM bytes per launch of `kernel` (captured in precision `prec`) from the
     committed ncu summary, if the kernel source has not changed since."""
@@ -446,8 +453,8 @@ def run_ours(args, rank, world, dist):
             # own traffic and are reported beside it (stage_io_gbs, traffic)
             flops, nbytes = tensor_work[k]
             bound, achieved, peak, unit = "tensor", flops / dur / 1e12, split_peak, "TFLOP/s"
-            src = (f"{peak_kind} sustained BF16 {bf16_sust} TFLOP/s (MEASURED_PEAKS.json) / "
-                   f"{issued_factor} split products per useful flop")
+            src = (peak_label(peak_kind, f"sustained BF16 {bf16_sust} TFLOP/s") +
+                   f" / {issued_factor} split products per useful flop")
         else:
             # the roof reached first: FP64 flops at the FP64 peak or bytes at the copy bandwidth
             flops, nbytes = other_work.get(k, (float("nan"), float("nan")))
@@ -456,7 +463,7 @@ def run_ours(args, rank, world, dist):
                 src = "derived: 1.25 TFLOP/s FP64 nominal at 2070 MHz, scaled to the sampled clock"
             else:
                 bound, achieved, peak, unit = "hbm", nbytes / dur / 1e9, hbm_gbs, "GB/s"
-                src = f"{peak_kind} HBM copy (MEASURED_PEAKS.json)"
+                src = peak_label(peak_kind, f"HBM copy {hbm_gbs} GB/s")
         traffic = ncu_traffic(k, args.prec)
         r = {"kernel": k, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
              "frac": achieved / peak, "traffic": traffic, "peak_source": src, "ms_per_launch": dur * 1e3}
@@ -1109,7 +1116,7 @@ def run_h64(args, rank, world, dist):
                       "issued_frac_of_bf16_sustained": useful * exec_frac * issued / (sigma_ms * 1e-3) / 1e12
                       / bf16_sust,
                       "useful_equiv_frac_of_bf16_sustained": useful * issued / (sigma_ms * 1e-3) / 1e12 / bf16_sust,
-                      "peak_source": f"{peak_kind} sustained BF16 {bf16_sust} TFLOP/s (MEASURED_PEAKS.json)"},
+                      "peak_source": peak_label(peak_kind, f"sustained BF16 {bf16_sust} TFLOP/s")},
             "fp64_gpu_path": {"sigma_s_per_iter": fp64_s_per_iter, "sample": f"points {pts}"},
             "speedup_split_vs_fp64_sigma": fp64_s_per_iter / (sigma_ms * 1e-3),
             "kernels": prof_ms, "gpu_launches": launches, "clocks": clocks,

@@ -5,6 +5,7 @@ gf2_sigma_tau_df) against the oracle's density-fitted Sigma (oracle/df.py).
   random factors, N = 5 .. 70 (ragged 64-wide GEMM tiles) and m = 1 .. 192;
 * N = 64 with m = 192 over 129 grid points: three chunks of the workspace,
   the last ragged, checked at every chunk boundary; N = 128 with m = 384;
+* a context on the power mesh (the mirrored G(-tau) of a non-equidistant grid);
 * the H32 lattice (6-31G, N = 64) with the even-tempered auxiliary set
   (m = 192) and a physical G(tau); the split-precision four-stage path on the
   same fitted integrals;
@@ -117,6 +118,24 @@ def test_largest_basis_n128(g):
     for j, k in enumerate((7, 8)):
         ref = osg.sigma_factored(G[k], osg.gbar_from_grid(G, k), v, W)
         assert np.abs(got[j] - ref).max() <= 1e-12 * np.abs(ref).max(), k
+
+
+def test_factor_order_on_the_power_mesh(g):
+    """A context on the non-equidistant grid: G(-tau_k) = -G(tau_{n_tau-1-k})
+    through the mesh's mirror symmetry, every mesh point against the oracle."""
+    from oracle import grids
+    M, idx = grids.power_mesh(4, 8)
+    n, m = 12, 30
+    n_tau = len(idx)
+    G = gi.random_symmetric_g(n, n_tau, seed=12)
+    B = _factor(m, n, 13)
+    ref = odf.sigma_tau_df(G, B)
+    with g.Context(n, None, 64, 20.0, grid=(M, idx)) as ctx:
+        g.gf2_set_df_integrals(ctx.handle, dev(B))
+        o = torch.zeros(n_tau, n, n, dtype=torch.float64, device="cuda")
+        g.gf2_sigma_tau_df(ctx.handle, dev(G), 0, n_tau, o, 0)
+        got = host(o)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_h32_lattice_with_the_even_tempered_fit(g):

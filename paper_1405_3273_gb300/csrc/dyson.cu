@@ -321,7 +321,7 @@ __device__ void mu_brent_start(MuState *s) {
 __device__ void mu_init(MuState *s, double mu0, double n_elec, double tol, int max_iter, int n_iw, int n_coarse) {
   s->n_elec = n_elec;
   s->tol = tol;
-  s->tol_coarse = fmax(tol, 1e-8);  // the coarse count itself is ~5e-8 off the full one
+  s->tol_coarse = fmax(tol, 1e-9);
   s->max_iter = max_iter;
   s->cap_coarse = 60;
   s->n_iw = n_iw;

@@ -1,8 +1,8 @@
 // Matsubara <-> imaginary-time transforms (the FFT steps of the GF2 loop).
 //
 // Both directions run one M-point complex FFT per matrix element in shared
-// memory (radix-2, decimation in frequency, bit-reversed output read back
-// through __brev), E adjacent elements per CTA so that every global access
+// memory (decimation in frequency in radix-4 passes, bit-reversed output read
+// back through __brev), E adjacent elements per CTA so that every global access
 // of a frequency or time row touches E*16 contiguous bytes.
 //
 // iw -> tau:  X(tau_k) = (2/beta) Re[e^{-i pi k/M} Z_k] + T(tau_k),
@@ -178,22 +178,51 @@ __global__ void pole_resum_kernel(int n_iw, const double2 *iw_pole, double *out)
   if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
-// In-place radix-2 DIF FFT of E sequences of length M in shared memory.
+// In-place DIF FFT of E sequences of length M in shared memory.
 // sign = -1: X_k = sum_j x_j e^{-2 pi i jk/M};  sign = +1: e^{+...}.
-// Output in bit-reversed order.
+// Output in bit-reversed order.  Each pass applies two radix-2 stages at once
+// (groups of 2 half, quarters q = half/2): the four values x[b], x[b+q],
+// x[b+half], x[b+half+q] go through the stage-`half` butterflies (twiddles of
+// positions p and p+q) and then the stage-`q` butterflies (twiddle of position
+// p at twice the stride), the same operations in the same order as two
+// radix-2 stages, with half the barriers and shared-memory round trips.  When
+// log2 M is odd a last radix-2 stage (half = 1) follows.
 __device__ void fft_dif_smem(double2 *x, int E, int M, const double2 *tw, int sign) {
-  const int halfM = M >> 1;
-  for (int half = halfM, tstride = 1; half >= 1; half >>= 1, tstride <<= 1) {
+  const int quarterM = M >> 2;
+  int half = M >> 1, tstride = 1;
+  for (; half >= 2; half >>= 2, tstride <<= 2) {
+    const int q = half >> 1;
+    for (int idx = threadIdx.x; idx < E * quarterM; idx += blockDim.x) {
+      const int e = idx / quarterM, j = idx - e * quarterM;
+      const int grp = j / q, p = j - grp * q;
+      const int b = grp * 2 * half + p;
+      double2 wa0 = tw[p * tstride], wa1 = tw[(p + q) * tstride], wb = tw[2 * p * tstride];
+      if (sign > 0) {
+        wa0.y = -wa0.y;
+        wa1.y = -wa1.y;
+        wb.y = -wb.y;
+      }
+      double2 *xe = x + (size_t)e * M;
+      const double2 x0 = xe[b], x1 = xe[b + q], x2 = xe[b + half], x3 = xe[b + half + q];
+      const double2 y0 = cadd(x0, x2), y2 = cmul(csub(x0, x2), wa0);
+      const double2 y1 = cadd(x1, x3), y3 = cmul(csub(x1, x3), wa1);
+      xe[b] = cadd(y0, y1);
+      xe[b + q] = cmul(csub(y0, y1), wb);
+      xe[b + half] = cadd(y2, y3);
+      xe[b + half + q] = cmul(csub(y2, y3), wb);
+    }
+    __syncthreads();
+  }
+  if (half == 1) {  // tstride = M / 2: every twiddle is tw[0]
+    const int halfM = M >> 1;
     for (int idx = threadIdx.x; idx < E * halfM; idx += blockDim.x) {
       const int e = idx / halfM, j = idx - e * halfM;
-      const int grp = j / half, pos = j - grp * half;
-      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-      double2 w = tw[pos * tstride];
+      double2 w = tw[0];
       if (sign > 0) w.y = -w.y;
       double2 *xe = x + (size_t)e * M;
-      const double2 a = xe[i0], b = xe[i1];
-      xe[i0] = cadd(a, b);
-      xe[i1] = cmul(csub(a, b), w);
+      const double2 a = xe[2 * j], b = xe[2 * j + 1];
+      xe[2 * j] = cadd(a, b);
+      xe[2 * j + 1] = cmul(csub(a, b), w);
     }
     __syncthreads();
   }

@@ -238,7 +238,7 @@ __global__ void pole_fold_kernel(int M, int n_iw, const double2 *__restrict__ iw
   for (int r = 0; r < 4; ++r) fold[4 * (size_t)j + r] = q[r];
 }
 
-__global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, double beta,
+__global__ void __launch_bounds__(512, 3) iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, double beta,
                                  const double2 *__restrict__ X_iw, const double *__restrict__ coef,
                                  const double2 *__restrict__ pole_fold, const double *__restrict__ tau_pole,
                                  const double2 *__restrict__ tw, const double2 *__restrict__ halfphase,
@@ -288,7 +288,7 @@ __global__ void iw_to_tau_kernel(int N2, int M, int log2M, int n_iw, int E, doub
   }
 }
 
-__global__ void tau_to_iw_kernel(int N2, int M, int log2M, int n_iw, int E,
+__global__ void __launch_bounds__(512, 3) tau_to_iw_kernel(int N2, int M, int log2M, int n_iw, int E,
                                  const double *__restrict__ X_tau, const double2 *__restrict__ tw,
                                  const double2 *__restrict__ halfphase, const double2 *__restrict__ t2w_w,
                                  const double2 *__restrict__ t2w_corr, double2 *__restrict__ X_iw) {
